@@ -1,0 +1,162 @@
+/*
+ * fc2t2.h -- C ABI of the GB300 (sm_103a) FC2T2 transform library.
+ *
+ * The library computes the multi-level uniform-grid Taylor transform of
+ * Lange & Kutz, "FC^2T^2: The Fast Continuous Convolutional Taylor Transform"
+ * (arXiv 2111.00110):
+ *
+ *     y_m  ~=  sum_n psi(p_n - q_m) w_n                       (Sec. 3, Eq. 1)
+ *
+ * for N sources p_n with weights w_n and M queries q_m in D = 2 or 3 dimensions,
+ * by P2M -> M2M -> M2L -> L2L -> L2P on a uniform grid (Sec. 3), truncated at total
+ * degree rho (Sec. 3, Eq. 2), and its adjoints with respect to w and p (Sec. 4.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Every array pointer is a DEVICE pointer owned by the caller, unless stated.
+ *    Inputs are never modified.  Arrays are dense, row-major, float32:
+ *      p    [N][dim]   source positions        w     [N]       source weights
+ *      q    [M][dim]   query positions         y     [M]       transform values
+ *      ybar [M]        cotangent of y          wbar  [N]       dL/dw
+ *      pbar [N][dim]   dL/dp
+ *    (one channel; see fc2t2_plan_desc.channels).
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
+ *    Calls are asynchronous with respect to the host: they enqueue kernels on
+ *    `stream` and return.  The only host synchronisation is in fc2t2_plan_create and,
+ *    when check_domain is set, at the end of fc2t2_forward / fc2t2_backward.
+ *  - A plan owns its operator tables and its device workspace; calls on one plan must
+ *    not overlap in time (enqueue them on one stream).  Different plans are independent.
+ *  - Every function returns a status code; nothing aborts or throws across the ABI.
+ *    fc2t2_last_error() returns the text of the last failure on the calling thread.
+ *  - Domain: [lo, hi)^dim.  The cell of a coordinate x at a level with n cells per
+ *    dimension is decided in FP32: t = (x - lo) * (n / (hi - lo)), cell = floor(t),
+ *    clamped to [0, n-1], each step rounded to FP32.  Points outside the domain are
+ *    clamped into the edge cell, or rejected with FC2T2_ERR_DOMAIN when check_domain
+ *    is set (the paper requires points inside the domain, Sec. 3.2).
+ */
+#ifndef FC2T2_H
+#define FC2T2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define FC2T2_API __attribute__((visibility("default")))
+#else
+#define FC2T2_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FC2T2_OK = 0,
+    FC2T2_ERR_INVALID_ARG = 1,   /* a NULL pointer, a size out of range, a bad descriptor */
+    FC2T2_ERR_UNSUPPORTED = 2,   /* a valid request this build does not implement */
+    FC2T2_ERR_OOM = 3,           /* device allocation failed in fc2t2_plan_create */
+    FC2T2_ERR_DOMAIN = 4,        /* check_domain set and a point lies outside [lo, hi)^dim */
+    FC2T2_ERR_CUDA = 5,          /* a CUDA runtime error (text in fc2t2_last_error) */
+    FC2T2_ERR_TIMEOUT = 6        /* a bounded device-side wait gave up */
+} fc2t2_status;
+
+typedef enum {
+    /* psi(x) = exp(-|x|^2 / (2 sigma^2)): the kernel of every experiment in the paper
+     * (Sec. 3.3, written there as exp(-alpha |x|^2), alpha = 1 / (2 sigma^2)). */
+    FC2T2_KERNEL_GAUSSIAN = 0,
+    /* psi(x) = sum_a c_a x^a, coefficients in graded multi-index order (degree, then the
+     * exponent of x_0 descending, then of x_1 descending); any degree.  For degree <= order
+     * the series is exact.  The backward pass assumes psi(-x) = psi(x) (Sec. 4.1). */
+    FC2T2_KERNEL_POLY = 1
+} fc2t2_kernel;
+
+typedef enum {
+    FC2T2_M2L_FP32 = 0,          /* M2L in FP32 on the CUDA cores */
+    FC2T2_M2L_TF32 = 1,          /* M2L on tcgen05 tensor cores, TF32 inputs, FP32 accumulate */
+    FC2T2_M2L_BF16 = 2           /* M2L on tcgen05 tensor cores, BF16 inputs, FP32 accumulate */
+} fc2t2_m2l_prec;
+
+typedef struct fc2t2_plan_s *fc2t2_plan;
+
+typedef struct {
+    int dim;                     /* 2 or 3 */
+    int grid;                    /* finest cells per dimension n: a power of two, 4 <= n <= 1024
+                                    (levels = log2(n) - 1, coarsest level 4 cells; Sec. 3.2) */
+    int order;                   /* rho, total-degree truncation, 1 <= rho <= 8 */
+    fc2t2_kernel kernel;
+    double sigma;                /* Gaussian width (> 0); ignored for FC2T2_KERNEL_POLY */
+    const double *poly_coef;     /* HOST pointer, n_poly coefficients; copied at plan creation */
+    int n_poly;                  /* must equal C(deg + dim, dim) for some degree deg */
+    double lo, hi;               /* domain [lo, hi)^dim, hi > lo */
+    int channels;                /* weights per source; this build supports 1 */
+    fc2t2_m2l_prec m2l;
+    int check_domain;            /* nonzero: reject points outside the domain (synchronises) */
+    int64_t max_sources;         /* workspace bound on N (>= 0) */
+    int64_t max_queries;         /* workspace bound on M (>= 0) */
+} fc2t2_plan_desc;
+
+/* Build a plan: validate `desc`, build the M2L / M2M / L2L operator tables in FP64 on
+ * the host (Sec. 3: the kernel derivatives are a once-per-plan preprocessing step, cf.
+ * Sec. 3.1), cast them to the M2L precision, and allocate the device workspace for
+ * max_sources / max_queries points.  Synchronises the current device.
+ * On success *out receives the plan; on failure *out is set to NULL.
+ * Errors: INVALID_ARG (desc or out NULL, values out of range), UNSUPPORTED
+ * (channels != 1, an M2L precision this build lacks), OOM, CUDA. */
+FC2T2_API fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out);
+
+/* Release a plan and its device memory.  NULL is accepted and ignored.  The caller
+ * must make sure no call on the plan is still running on the device. */
+FC2T2_API fc2t2_status fc2t2_plan_destroy(fc2t2_plan plan);
+
+/* Forward transform (Sec. 3): y[m] = sum_n psi(p[n] - q[m]) w[n] through the series.
+ * 0 <= N <= max_sources, 0 <= M <= max_queries; N = 0 gives y = 0.  y must not alias
+ * an input.  Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
+FC2T2_API fc2t2_status fc2t2_forward(fc2t2_plan plan, void *stream,
+                           const float *p, const float *w, int64_t N,
+                           const float *q, int64_t M, float *y);
+
+/* Backward pass of y = forward(p, w, q) for a cotangent ybar (Sec. 4.1):
+ *   wbar[n]    = sum_m psi(q[m] - p[n]) ybar[m]             (the transposed transform)
+ *   pbar[n][i] = w[n] * d/dx_i sum_m psi(x - q[m]) ybar[m] at x = p[n]
+ * computed as a second transform with sources q, weights ybar and targets p, whose local
+ * series is evaluated (wbar) and differentiated (pbar) at p with the binning of p held
+ * fixed.  Either output may be NULL to skip it.  The kernel must be even.
+ * Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
+FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
+                            const float *p, const float *w, int64_t N,
+                            const float *q, int64_t M, const float *ybar,
+                            float *wbar, float *pbar);
+
+/* Pipeline stages, for fc2t2_profile_read. */
+typedef enum {
+    FC2T2_STAGE_SORT = 0,        /* binning + counting sort of sources and queries */
+    FC2T2_STAGE_P2M = 1,
+    FC2T2_STAGE_M2M = 2,
+    FC2T2_STAGE_M2L = 3,
+    FC2T2_STAGE_L2L = 4,
+    FC2T2_STAGE_L2P = 5,         /* L2P, and the L2P gradient of the backward pass */
+    FC2T2_NUM_STAGES = 6
+} fc2t2_stage;
+
+/* Diagnostics, not part of the transform: while enabled, every call on `plan` records CUDA
+ * events around each stage's kernels on the call's stream.  The plan always counts the
+ * kernels it launches per stage.  Errors: INVALID_ARG (plan NULL), CUDA. */
+FC2T2_API fc2t2_status fc2t2_profile_enable(fc2t2_plan plan, int enable);
+
+/* Accumulated device time (ms, from the recorded events) and kernel launches per stage since
+ * the last reset; either array may be NULL, each holds FC2T2_NUM_STAGES entries.  Waits for the
+ * recorded events (synchronises with the streams they were recorded on).  reset != 0 clears
+ * the accumulators after reading.  Errors: INVALID_ARG, CUDA. */
+FC2T2_API fc2t2_status fc2t2_profile_read(fc2t2_plan plan, double *ms, int64_t *launches, int reset);
+
+/* Static text for a status code. */
+FC2T2_API const char *fc2t2_status_string(fc2t2_status status);
+
+/* Copy the message of the last failure on the calling thread into buf (NUL-terminated,
+ * truncated to n bytes) and return its status (FC2T2_OK if none). buf may be NULL. */
+FC2T2_API fc2t2_status fc2t2_last_error(char *buf, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC2T2_H */

@@ -1,0 +1,135 @@
+"""ctypes binding of the C ABI declared in ``include/fc2t2.h``.
+
+Argument marshalling only: every step of the transform runs in the CUDA library
+``_build/libfc2t2.so``.  Importing this module never falls back to anything else: if the
+library is missing, ``load()`` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libfc2t2.so")
+
+FC2T2_OK = 0
+STATUS = {
+    0: "FC2T2_OK",
+    1: "FC2T2_ERR_INVALID_ARG",
+    2: "FC2T2_ERR_UNSUPPORTED",
+    3: "FC2T2_ERR_OOM",
+    4: "FC2T2_ERR_DOMAIN",
+    5: "FC2T2_ERR_CUDA",
+    6: "FC2T2_ERR_TIMEOUT",
+}
+KERNELS = {"gaussian": 0, "poly": 1}
+M2L_PREC = {"fp32": 0, "tf32": 1, "bf16": 2}
+
+# every entry point declared in include/fc2t2.h
+EXPORTS = (
+    "fc2t2_plan_create",
+    "fc2t2_plan_destroy",
+    "fc2t2_forward",
+    "fc2t2_backward",
+    "fc2t2_status_string",
+    "fc2t2_last_error",
+    "fc2t2_profile_enable",
+    "fc2t2_profile_read",
+)
+STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p")
+
+
+class PlanDesc(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int),
+        ("grid", ctypes.c_int),
+        ("order", ctypes.c_int),
+        ("kernel", ctypes.c_int),
+        ("sigma", ctypes.c_double),
+        ("poly_coef", ctypes.POINTER(ctypes.c_double)),
+        ("n_poly", ctypes.c_int),
+        ("lo", ctypes.c_double),
+        ("hi", ctypes.c_double),
+        ("channels", ctypes.c_int),
+        ("m2l", ctypes.c_int),
+        ("check_domain", ctypes.c_int),
+        ("max_sources", ctypes.c_int64),
+        ("max_queries", ctypes.c_int64),
+    ]
+
+
+class FC2T2Error(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(
+                f"{path} is missing: build it with `python -m paper_2111_00110_gb300.build`")
+        lib = ctypes.CDLL(path)
+        vp, i64 = ctypes.c_void_p, ctypes.c_int64
+        lib.fc2t2_plan_create.argtypes = [ctypes.POINTER(PlanDesc), ctypes.POINTER(ctypes.c_void_p)]
+        lib.fc2t2_plan_destroy.argtypes = [vp]
+        lib.fc2t2_forward.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp]
+        lib.fc2t2_backward.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp, vp]
+        lib.fc2t2_status_string.argtypes = [ctypes.c_int]
+        lib.fc2t2_status_string.restype = ctypes.c_char_p
+        lib.fc2t2_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
+        lib.fc2t2_profile_enable.argtypes = [vp, ctypes.c_int]
+        lib.fc2t2_profile_read.argtypes = [vp, vp, vp, ctypes.c_int]
+        for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
+                     "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def check(status: int):
+    if status != FC2T2_OK:
+        lib = load()
+        buf = ctypes.create_string_buffer(512)
+        lib.fc2t2_last_error(buf, 512)
+        raise FC2T2Error(status, buf.value.decode(errors="replace"))
+
+
+def plan_create(desc: PlanDesc) -> int:
+    out = ctypes.c_void_p()
+    check(load().fc2t2_plan_create(ctypes.byref(desc), ctypes.byref(out)))
+    return out.value
+
+
+def plan_destroy(plan: int) -> None:
+    check(load().fc2t2_plan_destroy(plan))
+
+
+def forward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, y: int) -> None:
+    check(load().fc2t2_forward(plan, stream, p, w, N, q, M, y))
+
+
+def backward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int,
+             wbar: int, pbar: int) -> None:
+    check(load().fc2t2_backward(plan, stream, p, w, N, q, M, ybar, wbar, pbar))
+
+
+def profile_enable(plan: int, enable: bool) -> None:
+    check(load().fc2t2_profile_enable(plan, 1 if enable else 0))
+
+
+def profile_read(plan: int, reset: bool = False):
+    """Per-stage accumulated device milliseconds and kernel launches (dicts by stage name)."""
+    ms = (ctypes.c_double * len(STAGES))()
+    n = (ctypes.c_int64 * len(STAGES))()
+    check(load().fc2t2_profile_read(plan, ctypes.addressof(ms), ctypes.addressof(n), 1 if reset else 0))
+    return dict(zip(STAGES, list(ms))), dict(zip(STAGES, list(n)))

@@ -1,0 +1,509 @@
+// C ABI of the FC2T2 library: plan creation (operator tables, workspace) and the
+// forward / backward pipelines (Sec. 3 and Sec. 4.1 of arXiv 2111.00110).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fc2t2_internal.cuh"
+
+namespace fc2t2 {
+
+static thread_local fc2t2_status g_err_code = FC2T2_OK;
+static thread_local std::string g_err_msg;
+
+fc2t2_status set_error(fc2t2_status st, const std::string &msg) {
+    g_err_code = st;
+    g_err_msg = msg;
+    return st;
+}
+
+fc2t2_status check_cuda(cudaError_t e, const char *what) {
+    if (e == cudaSuccess) return FC2T2_OK;
+    return set_error(FC2T2_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+// ------------------------------------------------------------ host operator tables
+
+struct HostIndex {
+    int D = 0, rho = 0, P = 0;
+    std::vector<int> e;      // [P][3]
+    std::vector<int> deg;    // [P]
+    HostIndex(int D_, int rho_) : D(D_), rho(rho_), P(ncoef(D_, rho_)), e(3 * P, 0), deg(P, 0) {
+        for (int k = 0; k < P; ++k) {
+            // invert the graded index by search (tiny)
+            for (int a0 = 0; a0 <= rho; ++a0)
+                for (int a1 = 0; a0 + a1 <= rho; ++a1)
+                    for (int a2 = 0; a0 + a1 + a2 <= rho; ++a2) {
+                        if (D == 2 && a2 != 0) continue;
+                        const int g = D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
+                        if (g == k) { e[3 * k] = a0; e[3 * k + 1] = a1; e[3 * k + 2] = a2; deg[k] = a0 + a1 + a2; }
+                    }
+        }
+    }
+    int index(int a0, int a1, int a2) const {
+        if (a0 < 0 || a1 < 0 || a2 < 0 || a0 + a1 + a2 > rho) return -1;
+        return D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
+    }
+};
+
+// h^j g^(j)(x) for g(x) = exp(-x^2 / (2 sigma^2)), j = 0..J, via the probabilists' Hermite
+// polynomials: g^(j)(x) = (-1/sigma)^j He_j(x/sigma) g(x),  He_{j+1}(v) = v He_j - j He_{j-1}.
+static void gaussian_scaled_derivs_1d(double sigma, double h, double x, int J, double *out) {
+    const double v = x / sigma, g = std::exp(-0.5 * v * v), r = -h / sigma;
+    double hem1 = 0.0, he = 1.0, f = 1.0;
+    for (int j = 0; j <= J; ++j) {
+        out[j] = f * he * g;
+        const double hn = v * he - j * hem1;
+        hem1 = he;
+        he = hn;
+        f *= r;
+    }
+}
+
+// Dt[m] = h^|m| d^m psi(c) for every graded m.
+static void scaled_derivs(const fc2t2_plan_s *pl, const HostIndex &ix, const double *c, double h,
+                          double *out) {
+    const int D = pl->D;
+    if (pl->desc.kernel == FC2T2_KERNEL_GAUSSIAN) {
+        double g[3][kMaxOrder + 1];
+        for (int d = 0; d < D; ++d) gaussian_scaled_derivs_1d(pl->desc.sigma, h, c[d], ix.rho, g[d]);
+        for (int k = 0; k < ix.P; ++k) {
+            double v = 1.0;
+            for (int d = 0; d < D; ++d) v *= g[d][ix.e[3 * k + d]];
+            out[k] = v;
+        }
+        return;
+    }
+    // polynomial psi = sum_a coef_a x^a  (graded coefficients of some degree pdeg)
+    int pdeg = 0;
+    while (ncoef(D, pdeg) < (int)pl->poly.size()) ++pdeg;
+    HostIndex px(D, pdeg);
+    for (int k = 0; k < ix.P; ++k) {
+        double acc = 0.0;
+        for (int a = 0; a < (int)pl->poly.size(); ++a) {
+            double term = pl->poly[a];
+            if (term == 0.0) continue;
+            for (int d = 0; d < D; ++d) {
+                const int ad = px.e[3 * a + d], md = ix.e[3 * k + d];
+                if (ad < md) { term = 0.0; break; }
+                double fall = 1.0;   // ad! / (ad - md)!
+                for (int t = ad - md + 1; t <= ad; ++t) fall *= t;
+                double pw = 1.0;
+                for (int t = 0; t < ad - md; ++t) pw *= c[d];
+                term *= fall * pw;
+            }
+            acc += term;
+        }
+        double hp = 1.0;
+        for (int t = 0; t < ix.deg[k]; ++t) hp *= h;
+        out[k] = acc * hp;
+    }
+}
+
+template <typename T>
+static fc2t2_status dev_alloc(T **p, size_t count, const char *what) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, sizeof(T) * count);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_error(FC2T2_ERR_OOM, std::string("cudaMalloc failed for ") + what);
+    }
+    return FC2T2_OK;
+}
+
+template <typename T>
+static fc2t2_status upload(T *dst, const std::vector<T> &src, const char *what) {
+    if (src.empty()) return FC2T2_OK;
+    return check_cuda(cudaMemcpy(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice), what);
+}
+
+static void free_sort(SortWork &w) {
+    cudaFree(w.count); cudaFree(w.start); cudaFree(w.key); cudaFree(w.rank);
+    cudaFree(w.perm); cudaFree(w.key_sorted); cudaFree(w.pts); cudaFree(w.wts);
+    w = SortWork();
+}
+
+static fc2t2_status alloc_sort(SortWork &w, int64_t cap, int64_t G0, int D) {
+    w.cap = cap;
+    fc2t2_status st;
+    if ((st = dev_alloc(&w.count, G0, "cell counts")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.start, G0 + 1, "cell starts")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.key, cap, "keys")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.rank, cap, "ranks")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.perm, cap, "permutation")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.key_sorted, cap, "sorted keys")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.pts, cap * D, "sorted points")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.wts, cap, "sorted weights")) != FC2T2_OK) return st;
+    return FC2T2_OK;
+}
+
+static void destroy(fc2t2_plan_s *pl) {
+    if (!pl) return;
+    for (auto &pr : pl->pending) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
+    for (auto e : pl->event_pool) cudaEventDestroy(e);
+    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
+    cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
+    cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
+    cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
+    cudaFree(pl->d_mma_ops);
+    free_sort(pl->src);
+    free_sort(pl->qry);
+    delete pl;
+}
+
+static fc2t2_status build_tables(fc2t2_plan_s *pl) {
+    const int D = pl->D, rho = pl->rho, P = pl->P, Pp = pl->Pp;
+    HostIndex ix(D, rho);
+    const int nofs = D == 3 ? 343 : 49;
+
+    // scaled kernel derivatives per level and offset o in {-3..3}^D
+    std::vector<float> dtab((size_t)pl->nlev * nofs * Pp, 0.0f);
+    std::vector<double> tmp(P);
+    for (int l = 0; l < pl->nlev; ++l) {
+        const double h = pl->lev[l].h;
+        for (int o = 0; o < nofs; ++o) {
+            double c[3] = {0, 0, 0};
+            int r = o;
+            for (int d = 0; d < D; ++d) { c[d] = (double)(r % 7 - 3) * h; r /= 7; }
+            scaled_derivs(pl, ix, c, h, tmp.data());
+            for (int k = 0; k < P; ++k) dtab[((size_t)l * nofs + o) * Pp + k] = (float)tmp[k];
+        }
+    }
+    // child re-centring: shift[ch][g] = prod_d s_d^(g_d) / g_d!,  s_d = +1/2 (odd child) or -1/2
+    std::vector<float> shift((size_t)(1 << D) * P);
+    for (int ch = 0; ch < (1 << D); ++ch)
+        for (int g = 0; g < P; ++g) {
+            double v = 1.0;
+            for (int d = 0; d < D; ++d) {
+                const double s = ((ch >> d) & 1) ? 0.5 : -0.5;
+                for (int t = 1; t <= ix.e[3 * g + d]; ++t) v *= s / t;
+            }
+            shift[(size_t)ch * P + g] = (float)v;
+        }
+    std::vector<float> pow2(P);
+    for (int k = 0; k < P; ++k) pow2[k] = (float)std::ldexp(1.0, -ix.deg[k]);
+
+    std::vector<int> m2m_start(P + 1), l2l_start(P + 1), m2l_start(P + 1);
+    std::vector<int2> m2m_pairs, l2l_pairs, m2l_pairs;
+    for (int a = 0; a < P; ++a) {
+        m2m_start[a] = (int)m2m_pairs.size();
+        for (int b = 0; b < P; ++b) {
+            const int g = ix.index(ix.e[3 * a] - ix.e[3 * b], ix.e[3 * a + 1] - ix.e[3 * b + 1],
+                                   ix.e[3 * a + 2] - ix.e[3 * b + 2]);
+            if (g >= 0) m2m_pairs.push_back(make_int2(b, g));
+        }
+        l2l_start[a] = (int)l2l_pairs.size();
+        for (int g = 0; g < P; ++g) {
+            const int dlt = ix.index(ix.e[3 * g] - ix.e[3 * a], ix.e[3 * g + 1] - ix.e[3 * a + 1],
+                                     ix.e[3 * g + 2] - ix.e[3 * a + 2]);
+            if (dlt >= 0) l2l_pairs.push_back(make_int2(g, dlt));
+        }
+        m2l_start[a] = (int)m2l_pairs.size();
+        for (int b = 0; b < P; ++b) {
+            if (ix.deg[a] + ix.deg[b] > rho) continue;
+            const int kb = ix.index(ix.e[3 * a] + ix.e[3 * b], ix.e[3 * a + 1] + ix.e[3 * b + 1],
+                                    ix.e[3 * a + 2] + ix.e[3 * b + 2]);
+            m2l_pairs.push_back(make_int2(b, kb));
+        }
+    }
+    m2m_start[P] = (int)m2m_pairs.size();
+    l2l_start[P] = (int)l2l_pairs.size();
+    m2l_start[P] = (int)m2l_pairs.size();
+
+    fc2t2_status st;
+    if ((st = dev_alloc(&pl->d_dtab, dtab.size(), "derivative tables")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_shift, shift.size(), "shift tables")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_pow2, pow2.size(), "scales")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_m2m_start, m2m_start.size(), "m2m index")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_m2m_pairs, m2m_pairs.size(), "m2m pairs")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_l2l_start, l2l_start.size(), "l2l index")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_l2l_pairs, l2l_pairs.size(), "l2l pairs")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_m2l_start, m2l_start.size(), "m2l index")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&pl->d_m2l_pairs, m2l_pairs.size(), "m2l pairs")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_dtab, dtab, "upload derivative tables")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_shift, shift, "upload shift tables")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_pow2, pow2, "upload scales")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_m2m_start, m2m_start, "upload m2m index")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_m2m_pairs, m2m_pairs, "upload m2m pairs")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_l2l_start, l2l_start, "upload l2l index")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_l2l_pairs, l2l_pairs, "upload l2l pairs")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_m2l_start, m2l_start, "upload m2l index")) != FC2T2_OK) return st;
+    if ((st = upload(pl->d_m2l_pairs, m2l_pairs, "upload m2l pairs")) != FC2T2_OK) return st;
+    return FC2T2_OK;
+}
+
+static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
+    if (!d) return set_error(FC2T2_ERR_INVALID_ARG, "desc is NULL");
+    if (d->dim != 2 && d->dim != 3) return set_error(FC2T2_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (d->grid < 4 || d->grid > 1024 || (d->grid & (d->grid - 1)))
+        return set_error(FC2T2_ERR_INVALID_ARG, "grid must be a power of two in [4, 1024]");
+    if (d->order < 1 || d->order > kMaxOrder)
+        return set_error(FC2T2_ERR_INVALID_ARG, "order must be in [1, 8]");
+    if (!(d->hi > d->lo) || !std::isfinite(d->lo) || !std::isfinite(d->hi))
+        return set_error(FC2T2_ERR_INVALID_ARG, "domain must satisfy lo < hi, both finite");
+    if (d->kernel == FC2T2_KERNEL_GAUSSIAN) {
+        if (!(d->sigma > 0.0) || !std::isfinite(d->sigma))
+            return set_error(FC2T2_ERR_INVALID_ARG, "sigma must be positive");
+    } else if (d->kernel == FC2T2_KERNEL_POLY) {
+        if (!d->poly_coef || d->n_poly < 1)
+            return set_error(FC2T2_ERR_INVALID_ARG, "polynomial kernel needs coefficients");
+        int deg = 0;
+        while (ncoef(d->dim, deg) < d->n_poly && deg < 64) ++deg;
+        if (ncoef(d->dim, deg) != d->n_poly)
+            return set_error(FC2T2_ERR_INVALID_ARG, "n_poly must be C(deg + dim, dim)");
+    } else {
+        return set_error(FC2T2_ERR_INVALID_ARG, "unknown kernel");
+    }
+    if (d->channels != 1) return set_error(FC2T2_ERR_UNSUPPORTED, "only channels == 1 is supported");
+    if (d->m2l != FC2T2_M2L_FP32) return set_error(FC2T2_ERR_UNSUPPORTED, "M2L precision not available");
+    if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||
+        d->max_queries > (int64_t)INT32_MAX)
+        return set_error(FC2T2_ERR_INVALID_ARG, "max_sources / max_queries out of range");
+    int64_t G = 1;
+    for (int i = 0; i < d->dim; ++i) G *= d->grid;
+    if (G > (int64_t)1 << 30) return set_error(FC2T2_ERR_INVALID_ARG, "grid too large");
+    return FC2T2_OK;
+}
+
+static fc2t2_status finish_flags(fc2t2_plan_s *pl, cudaStream_t s) {
+    if (!pl->desc.check_domain) return FC2T2_OK;
+    int flags = 0;
+    fc2t2_status st = check_cuda(cudaMemcpyAsync(&flags, pl->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s),
+                                 "read flags");
+    if (st != FC2T2_OK) return st;
+    st = check_cuda(cudaStreamSynchronize(s), "synchronise");
+    if (st != FC2T2_OK) return st;
+    if (flags & 1) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
+    return FC2T2_OK;
+}
+
+// ---------------------------------------------------------------- stage profiling
+
+static cudaEvent_t take_event(fc2t2_plan_s *pl) {
+    if (!pl->event_pool.empty()) {
+        cudaEvent_t e = pl->event_pool.back();
+        pl->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+    return e;
+}
+
+// Records an event pair around a stage's launches on the call's stream while profiling.
+struct StageScope {
+    fc2t2_plan_s *pl;
+    cudaStream_t s;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageScope(fc2t2_plan_s *pl_, cudaStream_t s_, int stage_) : pl(pl_), s(s_), stage(stage_) {
+        if (pl->profiling && (a = take_event(pl)) != nullptr) cudaEventRecord(a, s);
+    }
+    ~StageScope() {
+        if (!a) return;
+        cudaEvent_t b = take_event(pl);
+        if (!b) { pl->event_pool.push_back(a); return; }
+        cudaEventRecord(b, s);
+        pl->pending.push_back({stage, a, b});
+    }
+};
+
+// bin + sort points (weights optional) into a sort workspace
+static fc2t2_status sort_points(fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt,
+                                int64_t n, SortWork &w) {
+    StageScope scope(pl, s, FC2T2_STAGE_SORT);
+    fc2t2_status st;
+    if ((st = check_cuda(launch_bin_count(pl, s, x, n, w), "bin")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(pl, s, w.count, w.start, pl->lev[0].G), "scan")) != FC2T2_OK) return st;
+    return check_cuda(launch_scatter(pl, s, x, wt, n, w), "scatter");
+}
+
+// P2M .. L2L: expansion of sorted sources into finest-level local coefficients d_L (level 0)
+static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src) {
+    fc2t2_status st;
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_P2M);
+        if ((st = check_cuda(launch_p2m(pl, s, src, pl->d_M), "p2m")) != FC2T2_OK) return st;
+    }
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_M2M);
+        for (int l = 0; l + 1 < pl->nlev; ++l)
+            if ((st = check_cuda(launch_m2m(pl, s, l), "m2m")) != FC2T2_OK) return st;
+    }
+    for (int l = pl->nlev - 1; l >= 0; --l) {
+        {
+            StageScope scope(pl, s, FC2T2_STAGE_M2L);
+            if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
+        }
+        if (l + 1 < pl->nlev) {
+            StageScope scope(pl, s, FC2T2_STAGE_L2L);
+            if ((st = check_cuda(launch_l2l(pl, s, l), "l2l")) != FC2T2_OK) return st;
+        }
+    }
+    return FC2T2_OK;
+}
+
+}  // namespace fc2t2
+
+using namespace fc2t2;
+
+extern "C" {
+
+fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
+    if (!out) return set_error(FC2T2_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    fc2t2_status st = validate_desc(desc);
+    if (st != FC2T2_OK) return st;
+    fc2t2_plan_s *pl = new (std::nothrow) fc2t2_plan_s();
+    if (!pl) return set_error(FC2T2_ERR_OOM, "host allocation failed");
+    pl->desc = *desc;
+    if (desc->kernel == FC2T2_KERNEL_POLY) pl->poly.assign(desc->poly_coef, desc->poly_coef + desc->n_poly);
+    pl->desc.poly_coef = nullptr;
+    pl->D = desc->dim;
+    pl->n = desc->grid;
+    pl->rho = desc->order;
+    pl->P = ncoef(pl->D, pl->rho);
+    pl->Pp = pad4(pl->P);
+    int lg = 0;
+    while ((1 << lg) < pl->n) ++lg;
+    pl->nlev = lg - 1;
+    int64_t off = 0;
+    for (int l = 0; l < pl->nlev; ++l) {
+        Level &lv = pl->lev[l];
+        lv.n = pl->n >> l;
+        lv.G = 1;
+        for (int d = 0; d < pl->D; ++d) lv.G *= lv.n;
+        lv.off = off;
+        lv.h = (desc->hi - desc->lo) / lv.n;
+        off += lv.G;
+    }
+    pl->G_total = off;
+    pl->lo_f = (float)desc->lo;
+    pl->hi_f = (float)desc->hi;
+    pl->scale0_f = (float)((double)pl->n / (desc->hi - desc->lo));
+
+    if ((st = dev_alloc(&pl->d_M, (size_t)pl->G_total * pl->Pp, "moments")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = dev_alloc(&pl->d_L, (size_t)pl->G_total * pl->Pp, "locals")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = dev_alloc(&pl->d_flags, 4, "flags")) != FC2T2_OK) { destroy(pl); return st; }
+    const int64_t G0 = pl->lev[0].G;
+    int64_t tiles = (G0 + 4095) / 4096, tmp = 16;
+    while (tiles > 1) { tmp += 2 * tiles + 1; tiles = (tiles + 4095) / 4096; }
+    pl->scan_tmp_len = tmp;
+    if ((st = dev_alloc(&pl->d_scan_tmp, (size_t)tmp, "scan workspace")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = alloc_sort(pl->src, desc->max_sources, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = alloc_sort(pl->qry, desc->max_queries, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = build_tables(pl)) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = check_cuda(cudaMemset(pl->d_flags, 0, 4 * sizeof(int)), "clear flags")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = check_cuda(cudaDeviceSynchronize(), "plan build")) != FC2T2_OK) { destroy(pl); return st; }
+    *out = pl;
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_plan_destroy(fc2t2_plan plan) {
+    destroy(plan);
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                           const float *q, int64_t M, float *y) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (N < 0 || M < 0 || N > pl->src.cap || M > pl->qry.cap)
+        return set_error(FC2T2_ERR_INVALID_ARG, "N or M outside [0, max]");
+    if (M == 0) return FC2T2_OK;
+    if (!q || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    fc2t2_status st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if (N == 0) {
+        if ((st = check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y")) != FC2T2_OK) return st;
+        if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
+        return finish_flags(pl, s);
+    }
+    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
+    if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, y, nullptr), "l2p")) != FC2T2_OK) return st;
+    }
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                            const float *q, int64_t M, const float *ybar, float *wbar, float *pbar) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (N < 0 || M < 0 || N > pl->src.cap || M > pl->qry.cap)
+        return set_error(FC2T2_ERR_INVALID_ARG, "N or M outside [0, max]");
+    if (N == 0 || (!wbar && !pbar)) return FC2T2_OK;
+    if (!p || !w || (M > 0 && (!q || !ybar))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    fc2t2_status st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if (M == 0) {
+        if (wbar && (st = check_cuda(cudaMemsetAsync(wbar, 0, sizeof(float) * N, s), "zero wbar")) != FC2T2_OK) return st;
+        if (pbar && (st = check_cuda(cudaMemsetAsync(pbar, 0, sizeof(float) * N * pl->D, s), "zero pbar")) != FC2T2_OK) return st;
+        if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+        return finish_flags(pl, s);
+    }
+    // the transposed transform: sources q with weights ybar, targets p (Sec. 4.1)
+    if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
+    if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
+    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar, pbar), "l2p grad")) != FC2T2_OK) return st;
+    }
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_profile_enable(fc2t2_plan pl, int enable) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    pl->profiling = enable != 0;
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_profile_read(fc2t2_plan pl, double *ms, int64_t *launches, int reset) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    fc2t2_status st = FC2T2_OK;
+    for (auto &pr : pl->pending) {
+        float t = 0.0f;
+        if (st == FC2T2_OK) st = check_cuda(cudaEventSynchronize(pr.b), "profile sync");
+        if (st == FC2T2_OK) st = check_cuda(cudaEventElapsedTime(&t, pr.a, pr.b), "profile time");
+        pl->stage_ms[pr.stage] += t;
+        pl->event_pool.push_back(pr.a);
+        pl->event_pool.push_back(pr.b);
+    }
+    pl->pending.clear();
+    for (int i = 0; i < FC2T2_NUM_STAGES; ++i) {
+        if (ms) ms[i] = pl->stage_ms[i];
+        if (launches) launches[i] = pl->launches[i];
+        if (reset) { pl->stage_ms[i] = 0.0; pl->launches[i] = 0; }
+    }
+    return st;
+}
+
+const char *fc2t2_status_string(fc2t2_status st) {
+    switch (st) {
+        case FC2T2_OK: return "ok";
+        case FC2T2_ERR_INVALID_ARG: return "invalid argument";
+        case FC2T2_ERR_UNSUPPORTED: return "unsupported";
+        case FC2T2_ERR_OOM: return "out of device memory";
+        case FC2T2_ERR_DOMAIN: return "point outside the domain";
+        case FC2T2_ERR_CUDA: return "CUDA error";
+        case FC2T2_ERR_TIMEOUT: return "device wait timed out";
+    }
+    return "unknown status";
+}
+
+fc2t2_status fc2t2_last_error(char *buf, size_t n) {
+    if (buf && n > 0) {
+        std::snprintf(buf, n, "%s", g_err_msg.c_str());
+    }
+    return g_err_code;
+}
+
+}  // extern "C"

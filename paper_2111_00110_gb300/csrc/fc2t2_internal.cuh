@@ -1,0 +1,140 @@
+// Internal definitions of the FC2T2 CUDA library: the plan, multi-index arithmetic,
+// the FP32 binning rule, and the kernel launchers shared between translation units.
+//
+// Representation on the device (scaled per level, which keeps every coefficient O(1)):
+//   Mt_l[c](b) = sum_{i in c} w_i u_i^b / b!,        u_i = (p_i - z_l(c)) / h_l
+//   Lt_l[c](k) = h_l^|k| L_l[c](k)
+//   Dt_l[o](m) = h_l^|m| d^m psi(o h_l)              (o an integer cell offset)
+// so that, with the paper's unscaled M, L (Sec. 3):
+//   M2L  Lt(k) += (-1)^|k| sum_{|b| <= rho-|k|} Dt[o](k+b) Mt[t+o](b)
+//   M2M  Mt_{l+1}(a) = 2^-|a| sum_children sum_{b<=a} s^(a-b)/(a-b)! Mt_l(b),  s = +-1/2
+//   L2L  Lt_l(k) += sum_{g>=k} s^(g-k)/(g-k)! 2^-|g| Lt_{l+1}(g)
+//   L2P  y = sum_k Lt_0(k) u^k / k!,  grad y = (1/h_0) sum_k Lt_0(k + e_i) u^k / k!
+// Multi-indices are graded: degree, then the exponent of x_0 descending, then of x_1
+// descending.  Coefficient rows are padded to Pp = P rounded up to 4 floats (16 bytes).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/fc2t2.h"
+
+namespace fc2t2 {
+
+constexpr int kMaxDim = 3;
+constexpr int kMaxOrder = 8;
+constexpr int kMaxLevels = 10;
+
+__host__ __device__ constexpr int ncoef(int D, int rho) {
+    return D == 2 ? (rho + 1) * (rho + 2) / 2 : (rho + 1) * (rho + 2) * (rho + 3) / 6;
+}
+__host__ __device__ constexpr int pad4(int P) { return (P + 3) & ~3; }
+
+// graded index of an exponent tuple
+__host__ __device__ constexpr int gidx2(int a0, int a1) {
+    int d = a0 + a1;
+    return d * (d + 1) / 2 + (d - a0);
+}
+__host__ __device__ constexpr int gidx3(int a0, int a1, int a2) {
+    int d = a0 + a1 + a2, r = d - a0;
+    return d * (d + 1) * (d + 2) / 6 + r * (r + 1) / 2 + (r - a1);
+}
+template <int D>
+__host__ __device__ constexpr int gidx(int a0, int a1, int a2) {
+    return D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
+}
+
+// The FP32 binning rule (every step rounded to FP32, no contraction).
+__device__ __forceinline__ int cell_of(float x, float lo, float scale, int n) {
+    float t = __fmul_rn(__fsub_rn(x, lo), scale);
+    float f = floorf(t);
+    int c = 0;
+    if (f >= 0.0f) c = (f >= (float)n) ? n - 1 : (int)f;   // NaN and negatives -> 0
+    return c;
+}
+__device__ __forceinline__ bool outside(float x, float lo, float scale, int n) {
+    float t = __fmul_rn(__fsub_rn(x, lo), scale);
+    return !(t >= 0.0f && t < (float)n);
+}
+
+// One counting sort of points into finest-level cells.
+struct SortWork {
+    int64_t cap = 0;
+    int *count = nullptr;       // [G0]   points per cell
+    int *start = nullptr;       // [G0+1] exclusive prefix sum
+    int *key = nullptr;         // [cap]  cell of point i (input order)
+    int *rank = nullptr;        // [cap]  position of point i within its cell
+    int *perm = nullptr;        // [cap]  sorted position -> input index
+    int *key_sorted = nullptr;  // [cap]  cell of sorted point
+    float *pts = nullptr;       // [cap][D] sorted positions
+    float *wts = nullptr;       // [cap]  sorted weights
+};
+
+struct Level {
+    int n;              // cells per dimension
+    int64_t G;          // cells
+    int64_t off;        // first cell of this level in the concatenated coefficient arrays
+    double h;           // cell width
+};
+
+}  // namespace fc2t2
+
+struct fc2t2_plan_s {
+    fc2t2_plan_desc desc;
+    std::vector<double> poly;
+    int D = 0, n = 0, rho = 0, P = 0, Pp = 0, nlev = 0;
+    fc2t2::Level lev[fc2t2::kMaxLevels];
+    int64_t G_total = 0;
+    float lo_f = 0.f, hi_f = 0.f, scale0_f = 0.f;
+
+    // device memory
+    float *d_M = nullptr;         // [G_total][Pp]
+    float *d_L = nullptr;         // [G_total][Pp]
+    float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
+    float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
+    float *d_pow2 = nullptr;      // [P]  2^-|a|
+    int *d_m2m_start = nullptr;   // [P+1]  per a: pairs (b, a-b) with b <= a
+    int2 *d_m2m_pairs = nullptr;
+    int *d_l2l_start = nullptr;   // [P+1]  per k: pairs (g, g-k) with g >= k
+    int2 *d_l2l_pairs = nullptr;
+    int *d_m2l_start = nullptr;   // [P+1]  per k: pairs (b, k+b) with |b| <= rho-|k|
+    int2 *d_m2l_pairs = nullptr;
+    int *d_scan_tmp = nullptr;    // block sums of the prefix scan
+    int64_t scan_tmp_len = 0;
+    int *d_flags = nullptr;       // [4] device error flags
+    fc2t2::SortWork src, qry;
+    void *d_mma_ops = nullptr;    // tensor-core M2L operators (optional)
+    size_t mma_ops_bytes = 0;
+
+    // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage
+    mutable int64_t launches[FC2T2_NUM_STAGES] = {0, 0, 0, 0, 0, 0};
+    bool profiling = false;
+    struct EventPair { int stage; cudaEvent_t a, b; };
+    std::vector<EventPair> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double stage_ms[FC2T2_NUM_STAGES] = {0, 0, 0, 0, 0, 0};
+};
+
+namespace fc2t2 {
+
+// error reporting (thread-local message)
+fc2t2_status set_error(fc2t2_status st, const std::string &msg);
+fc2t2_status check_cuda(cudaError_t e, const char *what);
+
+// launchers (return cudaGetLastError() of the launch)
+cudaError_t launch_bin_count(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, int64_t n,
+                             SortWork &w);
+cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n);
+cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt,
+                           int64_t n, SortWork &w);
+cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, float *M0);
+cudaError_t launch_m2m(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
+                       float *val, float *grad_times_w);
+
+}  // namespace fc2t2

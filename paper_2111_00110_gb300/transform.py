@@ -1,0 +1,135 @@
+"""PyTorch front end of the FC2T2 transform (arXiv 2111.00110).
+
+``Plan`` wraps one ``fc2t2_plan`` of the C ABI; ``Plan.forward`` / ``Plan.backward`` pass
+CUDA tensors' device pointers and the current stream to ``fc2t2_forward`` /
+``fc2t2_backward``.  ``FC2T2Function`` is the explicit layer of Sec. 4 as a
+``torch.autograd.Function``: forward computes y = f(q; p, w), backward returns
+(pbar, wbar, None) from the transposed transform (Sec. 4.1).  PyTorch only allocates memory
+and supplies streams; every arithmetic step runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import capi
+
+
+def _ptr(t: Optional[torch.Tensor]) -> int:
+    return 0 if t is None else t.data_ptr()
+
+
+def _check_tensor(t: torch.Tensor, name: str, shape) -> None:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+class Plan:
+    """A transform plan: dimension, finest grid, order, kernel, domain, workspace bounds."""
+
+    def __init__(self, dim: int, grid: int, order: int, sigma: float = 0.05, *,
+                 kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
+                 lo: float = 0.0, hi: float = 1.0, m2l: str = "fp32", check_domain: bool = False,
+                 max_sources: int = 1 << 20, max_queries: int = 1 << 20, device=None):
+        self.dim, self.grid, self.order = dim, grid, order
+        self.sigma, self.kernel, self.lo, self.hi, self.m2l = sigma, kernel, lo, hi, m2l
+        self.max_sources, self.max_queries = int(max_sources), int(max_queries)
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        d = capi.PlanDesc()
+        d.dim, d.grid, d.order = dim, grid, order
+        d.kernel = capi.KERNELS[kernel]
+        d.sigma = float(sigma)
+        self._poly = None
+        if poly_coef is not None:
+            self._poly = np.ascontiguousarray(poly_coef, dtype=np.float64)
+            d.poly_coef = self._poly.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+            d.n_poly = int(self._poly.size)
+        d.lo, d.hi = float(lo), float(hi)
+        d.channels = 1
+        d.m2l = capi.M2L_PREC[m2l]
+        d.check_domain = 1 if check_domain else 0
+        d.max_sources, d.max_queries = self.max_sources, self.max_queries
+        with torch.cuda.device(self.device):
+            self._h = capi.plan_create(d)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            capi.plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def profile(self, enable: bool = True) -> None:
+        """Record per-stage CUDA events on every call (diagnostics)."""
+        capi.profile_enable(self._h, enable)
+
+    def profile_read(self, reset: bool = False):
+        """(ms per stage, kernel launches per stage) accumulated since the last reset."""
+        return capi.profile_read(self._h, reset)
+
+    def _stream(self) -> int:
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def forward(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """y[m] = sum_n psi(p[n] - q[m]) w[n] (Sec. 3, Eq. 1) through the series."""
+        N, M = p.shape[0], q.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", (N,))
+        _check_tensor(q, "q", (M, self.dim))
+        y = torch.empty(M, device=q.device, dtype=torch.float32) if out is None else out
+        _check_tensor(y, "y", (M,))
+        capi.forward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(y))
+        return y
+
+    def backward(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, ybar: torch.Tensor,
+                 need_w: bool = True, need_p: bool = True):
+        """(wbar, pbar) of Sec. 4.1 for the cotangent ybar; either may be skipped (None)."""
+        N, M = p.shape[0], q.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", (N,))
+        _check_tensor(q, "q", (M, self.dim))
+        _check_tensor(ybar, "ybar", (M,))
+        wbar = torch.empty(N, device=p.device, dtype=torch.float32) if need_w else None
+        pbar = torch.empty(N, self.dim, device=p.device, dtype=torch.float32) if need_p else None
+        capi.backward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar),
+                      _ptr(wbar), _ptr(pbar))
+        return wbar, pbar
+
+
+class FC2T2Function(torch.autograd.Function):
+    """y = f(q; p, w) with hand-written adjoints (Sec. 4.1); q is treated as data."""
+
+    @staticmethod
+    def forward(ctx, p, w, q, plan: Plan):
+        p, w, q = p.contiguous(), w.contiguous(), q.contiguous()
+        ctx.plan = plan
+        ctx.save_for_backward(p, w, q)
+        return plan.forward(p, w, q)
+
+    @staticmethod
+    def backward(ctx, ybar):
+        p, w, q = ctx.saved_tensors
+        need_p, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if not (need_p or need_w):
+            return None, None, None, None
+        wbar, pbar = ctx.plan.backward(p, w, q, ybar.contiguous(), need_w=need_w, need_p=need_p)
+        return pbar, wbar, None, None
+
+
+def fc2t2(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable explicit layer y = f(q; p, w) (Sec. 4)."""
+    return FC2T2Function.apply(p, w, q, plan)

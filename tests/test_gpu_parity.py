@@ -1,0 +1,247 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle, element by element.
+
+Tolerance for the FP32 path: relative L2 error <= 1e-5 against the oracle, and every element
+within 1e-4 of the largest output magnitude (FP32 arithmetic, unit roundoff 6e-8, summed over
+at most a few thousand terms per output with cancellation factors below 5).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_00110_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+REL_L2 = 1e-5
+ELEM = 1e-4
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def assert_close(got, ref, rel=REL_L2, elem=ELEM, what=""):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    assert got.shape == ref.shape, what
+    assert np.all(np.isfinite(got)), what
+    scale = max(np.abs(ref).max(), 1e-30)
+    err = rel_l2(got, ref)
+    assert err <= rel, f"{what}: rel-L2 {err:.3e} > {rel:.1e}"
+    worst = np.abs(got - ref).max() / scale
+    assert worst <= elem, f"{what}: max element error {worst:.3e} of max |ref|"
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2111_00110_gb300 import build
+    build.build()
+    from paper_2111_00110_gb300 import capi
+    return capi.load()
+
+
+def make_plan(dim, grid, order, sigma, N, M, **kw):
+    from paper_2111_00110_gb300.transform import Plan
+    return Plan(dim, grid, order, sigma, max_sources=max(N, 1), max_queries=max(M, 1), **kw)
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda() for a in arrs]
+
+
+def run_forward(plan, p, w, q):
+    P_, W_, Q_ = to_dev(p, w, q)
+    y = plan.forward(P_, W_, Q_)
+    torch.cuda.synchronize()
+    return y.cpu().numpy()
+
+
+def run_backward(plan, p, w, q, ybar):
+    P_, W_, Q_, YB = to_dev(p, w, q, ybar)
+    wbar, pbar = plan.backward(P_, W_, Q_, YB)
+    torch.cuda.synchronize()
+    return wbar.cpu().numpy(), pbar.cpu().numpy()
+
+
+def odesc(dim, grid, order, sigma, **kw):
+    return oracle.OracleDesc(dim=dim, grid=grid, order=order, sigma=sigma, **kw)
+
+
+def f64(*a):
+    return [np.asarray(x, dtype=np.float64) for x in a]
+
+
+# ------------------------------------------------------------------------------ forward
+
+def test_uniform2d_forward(lib):
+    """2D, N = M = 4096, sigma 0.05, 32x32, order 4 (the CPU-checkable workload)."""
+    wl = workloads.uniform2d()
+    plan = make_plan(2, wl.grid, wl.order, wl.sigma, wl.N, wl.M)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    yo = oracle.forward(odesc(2, wl.grid, wl.order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    assert_close(y, yo, what="uniform2d")
+    # and the truncation error against the exact sum is the oracle's (about 1.1e-2)
+    yd = oracle.direct(odesc(2, wl.grid, wl.order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    assert rel_l2(y, yd) <= 2e-2
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("order", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_every_order(lib, dim, order):
+    grid = 16 if dim == 3 else 32
+    wl = workloads.uniform(100 + 10 * dim + order, dim, 3001, 2503, grid, order, 0.06)
+    plan = make_plan(dim, grid, order, wl.sigma, wl.N, wl.M)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    yo = oracle.forward(odesc(dim, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    assert_close(y, yo, what=f"D{dim} rho{order}")
+
+
+@pytest.mark.parametrize("dim,grid", [(2, 4), (2, 8), (3, 4), (3, 8), (2, 128), (3, 32)])
+def test_grid_sizes(lib, dim, grid):
+    sigma = 2.0 / grid
+    wl = workloads.uniform(7 + grid, dim, 2000, 1500, grid, 4, sigma)
+    plan = make_plan(dim, grid, 4, sigma, wl.N, wl.M)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    yo = oracle.forward(odesc(dim, grid, 4, sigma), *f64(wl.p, wl.w, wl.q))
+    assert_close(y, yo, what=f"D{dim} n{grid}")
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_polynomial_kernel_is_exact(lib, dim):
+    """For a polynomial psi of degree <= rho the series equals the direct sum of Eq. 1."""
+    mis = oracle.multi_indices(dim, 4)
+    coef = np.zeros(len(mis))
+    for i, m in enumerate(mis):
+        if sum(m) in (0, 2, 4) and all(e % 2 == 0 for e in m):
+            coef[i] = 1.0 / (1 + i)
+    grid = 16
+    wl = workloads.uniform(55 + dim, dim, 1500, 1200, grid, 4, 0.1)
+    plan = make_plan(dim, grid, 4, 0.1, wl.N, wl.M, kernel="poly", poly_coef=coef)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    d = odesc(dim, grid, 4, 0.1, kernel="poly", poly_coef=coef)
+    yd = oracle.direct(d, *f64(wl.p, wl.w, wl.q))
+    assert_close(y, yd, rel=2e-5, elem=2e-4, what="poly")
+
+
+def test_clustered_sources_and_empty_cells(lib):
+    """All sources in a few cells (long segments), most cells empty."""
+    rng = np.random.default_rng(77)
+    p = (0.3 + 0.01 * rng.standard_normal((4000, 3))).clip(0, 0.999)
+    p[:1000] = 0.8 + 0.001 * rng.random((1000, 3))
+    w = rng.standard_normal(4000)
+    q = rng.random((3000, 3))
+    plan = make_plan(3, 16, 5, 0.05, 4000, 3000)
+    y = run_forward(plan, p, w, q)
+    yo = oracle.forward(odesc(3, 16, 5, 0.05), *f64(p.astype(np.float32), w.astype(np.float32),
+                                                  q.astype(np.float32)))
+    assert_close(y, yo, what="clustered")
+
+
+def test_points_on_faces_and_outside_are_clamped(lib):
+    """Coordinates on cell faces, at hi and outside [lo, hi) bin by the FP32 rule on both sides."""
+    rng = np.random.default_rng(5)
+    grid = 16
+    faces = rng.integers(0, grid + 1, size=(500, 3)) / grid
+    outside = rng.uniform(-0.2, 1.2, size=(300, 3))
+    p = np.concatenate([faces, outside, rng.random((700, 3))]).astype(np.float32)
+    w = rng.standard_normal(p.shape[0]).astype(np.float32)
+    q = np.concatenate([rng.random((600, 3)), faces[:200]]).astype(np.float32)
+    plan = make_plan(3, grid, 3, 0.08, p.shape[0], q.shape[0])
+    y = run_forward(plan, p, w, q)
+    yo = oracle.forward(odesc(3, grid, 3, 0.08), *f64(p, w, q))
+    assert_close(y, yo, what="faces")
+
+
+def test_check_domain_reports_points_outside(lib):
+    from paper_2111_00110_gb300 import capi
+    p = np.array([[0.5, 0.5, 0.5], [1.5, 0.2, 0.2]], dtype=np.float32)
+    w = np.ones(2, dtype=np.float32)
+    q = np.array([[0.1, 0.2, 0.3]], dtype=np.float32)
+    plan = make_plan(3, 8, 2, 0.1, 2, 1, check_domain=True)
+    with pytest.raises(capi.FC2T2Error) as e:
+        run_forward(plan, p, w, q)
+    assert e.value.status == 4
+    # inside points pass
+    y = run_forward(plan, p[:1], w[:1], q)
+    assert np.isfinite(y).all()
+
+
+def test_empty_inputs(lib):
+    plan = make_plan(3, 8, 3, 0.1, 10, 10)
+    rng = np.random.default_rng(1)
+    p, w, q = rng.random((10, 3)), rng.standard_normal(10), rng.random((10, 3))
+    y = run_forward(plan, p[:0], w[:0], q)
+    assert np.all(y == 0.0)
+    assert run_forward(plan, p, w, q[:0]).shape == (0,)
+    wbar, pbar = run_backward(plan, p, w, q[:0], np.zeros(0))
+    assert np.all(wbar == 0.0) and np.all(pbar == 0.0)
+
+
+def test_sizes_beyond_the_plan_are_rejected(lib):
+    from paper_2111_00110_gb300 import capi
+    plan = make_plan(2, 8, 2, 0.1, 10, 10)
+    rng = np.random.default_rng(2)
+    with pytest.raises(capi.FC2T2Error) as e:
+        run_forward(plan, rng.random((11, 2)), rng.random(11), rng.random((5, 2)))
+    assert e.value.status == 1
+
+
+def test_repeated_calls_are_consistent(lib):
+    wl = workloads.uniform(9, 3, 5000, 5000, 16, 4, 0.05)
+    plan = make_plan(3, 16, 4, 0.05, wl.N, wl.M)
+    y1 = run_forward(plan, wl.p, wl.w, wl.q)
+    y2 = run_forward(plan, wl.p, wl.w, wl.q)
+    assert rel_l2(y1, y2) <= 1e-6
+
+
+# ----------------------------------------------------------------------------- backward
+
+@pytest.mark.parametrize("dim,grid,order", [(2, 32, 4), (3, 16, 4), (3, 16, 6), (3, 8, 8)])
+def test_backward_small(lib, dim, grid, order):
+    wl = workloads.uniform(300 + grid + order, dim, 2100, 1900, grid, order, 0.06)
+    ybar = wl.ybar()
+    plan = make_plan(dim, grid, order, wl.sigma, wl.N, wl.M)
+    wbar, pbar = run_backward(plan, wl.p, wl.w, wl.q, ybar)
+    wo, po = oracle.backward(odesc(dim, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q, ybar))
+    assert_close(wbar, wo, what="wbar")
+    assert_close(pbar, po, what="pbar")
+
+
+def test_autograd_function_matches_backward(lib):
+    from paper_2111_00110_gb300.transform import fc2t2
+    wl = workloads.uniform(31, 3, 3000, 2000, 16, 4, 0.05)
+    plan = make_plan(3, 16, 4, 0.05, wl.N, wl.M)
+    P_, W_, Q_ = to_dev(wl.p, wl.w, wl.q)
+    P_.requires_grad_(True)
+    W_.requires_grad_(True)
+    y = fc2t2(P_, W_, Q_, plan)
+    loss = (y * y).sum()
+    loss.backward()
+    torch.cuda.synchronize()
+    yo = oracle.forward(odesc(3, 16, 4, 0.05), *f64(wl.p, wl.w, wl.q))
+    wo, po = oracle.backward(odesc(3, 16, 4, 0.05), *f64(wl.p, wl.w, wl.q), 2.0 * yo)
+    assert_close(W_.grad.cpu().numpy(), wo, what="autograd wbar")
+    assert_close(P_.grad.cpu().numpy(), po, what="autograd pbar")
+
+
+# ------------------------------------------------------------------------ full size
+
+@pytest.mark.slow
+def test_uniform3d_full_size_forward_backward(lib):
+    """3D, N = M = 2^20, sigma 0.02, 64^3, order 6: forward and backward of L = sum y^2,
+    against the oracle's full FP64 transform."""
+    wl = workloads.uniform3d()
+    plan = make_plan(3, wl.grid, wl.order, wl.sigma, wl.N, wl.M)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    d = odesc(3, wl.grid, wl.order, wl.sigma)
+    yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q))
+    assert_close(y, yo, what="uniform3d forward")
+    ybar = 2.0 * y.astype(np.float32)
+    wbar, pbar = run_backward(plan, wl.p, wl.w, wl.q, ybar)
+    rng = np.random.default_rng(2024)
+    sel = rng.choice(wl.N, size=4096, replace=False)
+    wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, ybar), sel=sel)
+    assert_close(wbar[sel], wo, what="uniform3d wbar")
+    assert_close(pbar[sel], po, what="uniform3d pbar")
