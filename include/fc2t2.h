@@ -148,6 +148,28 @@ FC2T2_API fc2t2_status fc2t2_profile_enable(fc2t2_plan plan, int enable);
  * the accumulators after reading.  Errors: INVALID_ARG, CUDA. */
 FC2T2_API fc2t2_status fc2t2_profile_read(fc2t2_plan plan, double *ms, int64_t *launches, int reset);
 
+/* Forward transform that allocates no device memory and needs no plan.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call cudaMalloc when they need
+ * the transform -- for example code inside a framework that owns all device memory through its
+ * own pool, or a real-time loop that must not allocate after start-up.
+ * It computes exactly what fc2t2_forward computes for a plan built from `desc` (same kernels),
+ * but keeps every intermediate (cell sort, coefficients of all levels, operator tables) in one
+ * static device array inside the library, about 6.1 MB, which every GPU that loads the library
+ * holds until the process exits.  Limits: Gaussian kernel, one channel, FP32 M2L,
+ * grid^dim <= 4096 finest cells (64^2 or 16^3), 1 <= order <= 4, 0 <= N, M <= 65536; larger
+ * requests return FC2T2_ERR_INVALID_ARG (or FC2T2_ERR_UNSUPPORTED for other kernels) before any
+ * work is queued.  desc->max_sources / max_queries / check_domain are ignored.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call outside any stream capture.  All calls share the array and it keeps the last
+ * call's contents (each call clears what must start from zero): calls whose work overlaps on
+ * the GPU -- on different streams or from different threads -- race and give wrong results, so
+ * issue them on one stream.  The call blocks until `stream` has finished earlier work (it copies
+ * the operator tables from host memory).  Pointers as for fc2t2_forward.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *desc, void *stream,
+                                             const float *p, const float *w, int64_t N,
+                                             const float *q, int64_t M, float *y);
+
 /* Static text for a status code. */
 FC2T2_API const char *fc2t2_status_string(fc2t2_status status);
 

@@ -36,6 +36,7 @@ EXPORTS = (
     "fc2t2_last_error",
     "fc2t2_profile_enable",
     "fc2t2_profile_read",
+    "fc2t2_forward_noalloc",
 )
 STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p")
 
@@ -89,8 +90,10 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_last_error.argtypes = [ctypes.c_char_p, ctypes.c_size_t]
         lib.fc2t2_profile_enable.argtypes = [vp, ctypes.c_int]
         lib.fc2t2_profile_read.argtypes = [vp, vp, vp, ctypes.c_int]
+        lib.fc2t2_forward_noalloc.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
-                     "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read"):
+                     "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
+                     "fc2t2_forward_noalloc"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib

@@ -1,0 +1,293 @@
+// fc2t2_forward_noalloc: the forward transform without any device allocation.
+//
+// Some callers cannot call cudaMalloc at the moment they need a transform: code running
+// inside a framework that owns all device memory through its own pool (and forbids foreign
+// allocations), real-time or embedded loops that must not allocate after start-up, and
+// callbacks that run while another component holds the allocator.  For them this entry
+// point needs no plan: everything the transform keeps between kernels (the cell sort, the
+// moment and local coefficients of every level, and the operator tables) lives in one
+// file-scope device array, sized for small problems (limits below).
+//
+// The array is part of the library image: every GPU that loads the library holds it
+// (kScratchBytes) until the process exits.  All calls share it, and it keeps the previous
+// call's contents; everything that must start from zero is cleared by the call itself.
+// Two calls whose work overlaps on the GPU (different streams, or different host threads)
+// race on the array and give wrong results: issue them on one stream, one after the other.
+//
+// The device address of the array is looked up once per device with cudaGetSymbolAddress
+// (host code cannot use the array's name as a device pointer); the first call on a device
+// does this set-up, so make the first call outside any CUDA stream capture.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+
+#include "fc2t2_internal.cuh"
+
+namespace fc2t2 {
+namespace {
+
+// Limits of the allocation-free path.
+constexpr int kNaMaxCells = 4096;          // finest cells: 64^2 in 2D, 16^3 in 3D
+constexpr int kNaMaxOrder = 4;             // P <= 35 (3D), Pp <= 36
+constexpr int64_t kNaMaxPoints = 65536;    // sources and queries, each
+constexpr int kNaMaxPp = 36;
+constexpr int kNaMaxLevels = 5;            // 64^2: 64, 32, 16, 8, 4
+constexpr int64_t kNaMaxCellsAllLevels = kNaMaxCells * 4 / 3 + 16;
+constexpr int kNaOffsets = 343;            // 7^3 cell offsets
+constexpr int kNaMaxPairs = 35 * 35;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+constexpr size_t kSortBytes =
+    align256(sizeof(int) * kNaMaxCells) + align256(sizeof(int) * (kNaMaxCells + 1)) +
+    4 * align256(sizeof(int) * kNaMaxPoints) + align256(sizeof(float) * kNaMaxPoints * 3) +
+    align256(sizeof(float) * kNaMaxPoints);
+constexpr size_t kScratchBytes =
+    2 * align256(sizeof(float) * kNaMaxCellsAllLevels * kNaMaxPp) +                  // M, L
+    align256(sizeof(float) * kNaMaxLevels * kNaOffsets * kNaMaxPp) +                 // dtab
+    align256(sizeof(float) * 8 * kNaMaxPp) + align256(sizeof(float) * kNaMaxPp) +    // shift, 2^-|a|
+    3 * (align256(sizeof(int) * (kNaMaxPp + 1)) + align256(sizeof(int2) * kNaMaxPairs)) +
+    align256(sizeof(int) * 64) + align256(sizeof(int) * 4) +                         // scan, flags
+    2 * kSortBytes;
+
+}  // namespace
+
+// The scratch array: kScratchBytes, about 6.1 MB.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+namespace {
+
+std::mutex g_na_mutex;                 // guards the host staging tables and the address cache
+void *g_na_addr[128] = {nullptr};      // device address of the scratch array, per device
+
+// host staging of the operator tables (static storage, no allocation)
+float h_dtab[kNaMaxLevels * kNaOffsets * kNaMaxPp];
+float h_shift[8 * kNaMaxPp];
+float h_pow2[kNaMaxPp];
+int h_start[3][kNaMaxPp + 1];
+int2 h_pairs[3][kNaMaxPairs];
+
+struct SmallIndex {
+    int D, rho, P;
+    int e[kNaMaxPp][3];
+    int deg[kNaMaxPp];
+    int index(int a0, int a1, int a2) const {
+        if (a0 < 0 || a1 < 0 || a2 < 0 || a0 + a1 + a2 > rho) return -1;
+        return D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
+    }
+};
+
+void small_index(int D, int rho, SmallIndex &ix) {
+    ix.D = D; ix.rho = rho; ix.P = ncoef(D, rho);
+    for (int a0 = 0; a0 <= rho; ++a0)
+        for (int a1 = 0; a0 + a1 <= rho; ++a1)
+            for (int a2 = 0; a0 + a1 + a2 <= rho; ++a2) {
+                if (D == 2 && a2) continue;
+                const int k = D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
+                ix.e[k][0] = a0; ix.e[k][1] = a1; ix.e[k][2] = a2; ix.deg[k] = a0 + a1 + a2;
+            }
+}
+
+// h^j g^(j)(x), g = exp(-x^2/(2 sigma^2)), probabilists' Hermite recurrence
+void gauss_1d(double sigma, double h, double x, int J, double *out) {
+    const double v = x / sigma, g = std::exp(-0.5 * v * v), r = -h / sigma;
+    double hem1 = 0.0, he = 1.0, f = 1.0;
+    for (int j = 0; j <= J; ++j) {
+        out[j] = f * he * g;
+        const double hn = v * he - j * hem1;
+        hem1 = he; he = hn; f *= r;
+    }
+}
+
+template <typename T>
+T *carve(unsigned char *base, size_t &off, size_t count) {
+    T *p = reinterpret_cast<T *>(base + off);
+    off += align256(sizeof(T) * count);
+    return p;
+}
+
+}  // namespace
+}  // namespace fc2t2
+
+using namespace fc2t2;
+
+extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *desc, void *stream,
+                                                        const float *p, const float *w, int64_t N,
+                                                        const float *q, int64_t M, float *y) {
+    if (!desc) return set_error(FC2T2_ERR_INVALID_ARG, "desc is NULL");
+    if (desc->dim != 2 && desc->dim != 3) return set_error(FC2T2_ERR_INVALID_ARG, "dim must be 2 or 3");
+    if (desc->kernel != FC2T2_KERNEL_GAUSSIAN)
+        return set_error(FC2T2_ERR_UNSUPPORTED, "the allocation-free path supports the Gaussian kernel only");
+    if (!(desc->sigma > 0.0) || !std::isfinite(desc->sigma))
+        return set_error(FC2T2_ERR_INVALID_ARG, "sigma must be positive");
+    if (!(desc->hi > desc->lo) || !std::isfinite(desc->lo) || !std::isfinite(desc->hi))
+        return set_error(FC2T2_ERR_INVALID_ARG, "domain must satisfy lo < hi");
+    if (desc->channels != 1 || desc->m2l != FC2T2_M2L_FP32)
+        return set_error(FC2T2_ERR_UNSUPPORTED, "the allocation-free path supports one channel, FP32 M2L");
+    if (desc->grid < 4 || (desc->grid & (desc->grid - 1)))
+        return set_error(FC2T2_ERR_INVALID_ARG, "grid must be a power of two >= 4");
+    int64_t cells = 1;
+    for (int d = 0; d < desc->dim; ++d) cells *= desc->grid;
+    if (cells > kNaMaxCells)
+        return set_error(FC2T2_ERR_INVALID_ARG,
+                         "allocation-free path: grid^dim exceeds 4096 cells (64^2 or 16^3); use a plan");
+    if (desc->order < 1 || desc->order > kNaMaxOrder)
+        return set_error(FC2T2_ERR_INVALID_ARG, "allocation-free path: order must be in [1, 4]; use a plan");
+    if (N < 0 || M < 0 || N > kNaMaxPoints || M > kNaMaxPoints)
+        return set_error(FC2T2_ERR_INVALID_ARG,
+                         "allocation-free path: N and M must be in [0, 65536]; use a plan");
+    if (M == 0) return FC2T2_OK;
+    if (!q || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    int dev = 0;
+    fc2t2_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (st != FC2T2_OK) return st;
+    if (dev < 0 || dev >= 128) return set_error(FC2T2_ERR_UNSUPPORTED, "device ordinal too large");
+    if (!g_na_addr[dev]) {
+        void *addr = nullptr;
+        st = check_cuda(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress");
+        if (st != FC2T2_OK) return st;
+        g_na_addr[dev] = addr;
+    }
+    unsigned char *base = static_cast<unsigned char *>(g_na_addr[dev]);
+
+    // a plan on the stack whose device pointers all point into the scratch array
+    fc2t2_plan_s pl;
+    pl.desc = *desc;
+    pl.desc.poly_coef = nullptr;
+    pl.D = desc->dim;
+    pl.n = desc->grid;
+    pl.rho = desc->order;
+    pl.P = ncoef(pl.D, pl.rho);
+    pl.Pp = pad4(pl.P);
+    int lg = 0;
+    while ((1 << lg) < pl.n) ++lg;
+    pl.nlev = lg - 1;
+    int64_t off_cells = 0;
+    for (int l = 0; l < pl.nlev; ++l) {
+        Level &lv = pl.lev[l];
+        lv.n = pl.n >> l;
+        lv.G = 1;
+        for (int d = 0; d < pl.D; ++d) lv.G *= lv.n;
+        lv.off = off_cells;
+        lv.h = (desc->hi - desc->lo) / lv.n;
+        off_cells += lv.G;
+    }
+    pl.G_total = off_cells;
+    pl.lo_f = (float)desc->lo;
+    pl.hi_f = (float)desc->hi;
+    pl.scale0_f = (float)((double)pl.n / (desc->hi - desc->lo));
+
+    size_t off = 0;
+    pl.d_M = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
+    pl.d_L = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
+    pl.d_dtab = carve<float>(base, off, (size_t)kNaMaxLevels * kNaOffsets * kNaMaxPp);
+    pl.d_shift = carve<float>(base, off, 8 * kNaMaxPp);
+    pl.d_pow2 = carve<float>(base, off, kNaMaxPp);
+    int *starts[3];
+    int2 *pairs[3];
+    for (int t = 0; t < 3; ++t) {
+        starts[t] = carve<int>(base, off, kNaMaxPp + 1);
+        pairs[t] = carve<int2>(base, off, kNaMaxPairs);
+    }
+    pl.d_m2m_start = starts[0]; pl.d_m2m_pairs = pairs[0];
+    pl.d_l2l_start = starts[1]; pl.d_l2l_pairs = pairs[1];
+    pl.d_m2l_start = starts[2]; pl.d_m2l_pairs = pairs[2];
+    pl.d_scan_tmp = carve<int>(base, off, 64);
+    pl.d_flags = carve<int>(base, off, 4);
+    SortWork *sorts[2] = {&pl.src, &pl.qry};
+    for (SortWork *sw : sorts) {
+        sw->cap = kNaMaxPoints;
+        sw->count = carve<int>(base, off, kNaMaxCells);
+        sw->start = carve<int>(base, off, kNaMaxCells + 1);
+        sw->key = carve<int>(base, off, kNaMaxPoints);
+        sw->rank = carve<int>(base, off, kNaMaxPoints);
+        sw->perm = carve<int>(base, off, kNaMaxPoints);
+        sw->key_sorted = carve<int>(base, off, kNaMaxPoints);
+        sw->pts = carve<float>(base, off, kNaMaxPoints * 3);
+        sw->wts = carve<float>(base, off, kNaMaxPoints);
+    }
+    if (off > kScratchBytes) return set_error(FC2T2_ERR_UNSUPPORTED, "scratch layout exceeds the array");
+
+    // operator tables (the same definitions as a plan's), staged in static host memory
+    SmallIndex ix;
+    small_index(pl.D, pl.rho, ix);
+    const int P = pl.P, Pp = pl.Pp, D = pl.D, nofs = D == 3 ? 343 : 49;
+    std::memset(h_dtab, 0, sizeof(float) * (size_t)pl.nlev * nofs * Pp);
+    for (int l = 0; l < pl.nlev; ++l) {
+        const double h = pl.lev[l].h;
+        for (int o = 0; o < nofs; ++o) {
+            double g[3][kNaMaxOrder + 1];
+            int r = o;
+            for (int d = 0; d < D; ++d) { gauss_1d(desc->sigma, h, (double)(r % 7 - 3) * h, pl.rho, g[d]); r /= 7; }
+            for (int k = 0; k < P; ++k) {
+                double v = 1.0;
+                for (int d = 0; d < D; ++d) v *= g[d][ix.e[k][d]];
+                h_dtab[((size_t)l * nofs + o) * Pp + k] = (float)v;
+            }
+        }
+    }
+    for (int ch = 0; ch < (1 << D); ++ch)
+        for (int gg = 0; gg < P; ++gg) {
+            double v = 1.0;
+            for (int d = 0; d < D; ++d) {
+                const double sg = ((ch >> d) & 1) ? 0.5 : -0.5;
+                for (int t = 1; t <= ix.e[gg][d]; ++t) v *= sg / t;
+            }
+            h_shift[ch * P + gg] = (float)v;
+        }
+    for (int k = 0; k < P; ++k) h_pow2[k] = (float)std::ldexp(1.0, -ix.deg[k]);
+    int cnt[3] = {0, 0, 0};
+    for (int a = 0; a < P; ++a) {
+        h_start[0][a] = cnt[0];
+        for (int b = 0; b < P; ++b) {
+            const int gg = ix.index(ix.e[a][0] - ix.e[b][0], ix.e[a][1] - ix.e[b][1], ix.e[a][2] - ix.e[b][2]);
+            if (gg >= 0) h_pairs[0][cnt[0]++] = make_int2(b, gg);
+        }
+        h_start[1][a] = cnt[1];
+        for (int gg = 0; gg < P; ++gg) {
+            const int dl = ix.index(ix.e[gg][0] - ix.e[a][0], ix.e[gg][1] - ix.e[a][1], ix.e[gg][2] - ix.e[a][2]);
+            if (dl >= 0) h_pairs[1][cnt[1]++] = make_int2(gg, dl);
+        }
+        h_start[2][a] = cnt[2];
+        for (int b = 0; b < P; ++b) {
+            if (ix.deg[a] + ix.deg[b] > pl.rho) continue;
+            h_pairs[2][cnt[2]++] = make_int2(b, ix.index(ix.e[a][0] + ix.e[b][0], ix.e[a][1] + ix.e[b][1],
+                                                         ix.e[a][2] + ix.e[b][2]));
+        }
+    }
+    for (int t = 0; t < 3; ++t) h_start[t][P] = cnt[t];
+
+    // pageable host-to-device copies return once the host data has been staged
+    struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
+        {pl.d_dtab, h_dtab, sizeof(float) * (size_t)pl.nlev * nofs * Pp},
+        {pl.d_shift, h_shift, sizeof(float) * (size_t)(1 << D) * P},
+        {pl.d_pow2, h_pow2, sizeof(float) * (size_t)P},
+        {starts[0], h_start[0], sizeof(int) * (size_t)(P + 1)}, {pairs[0], h_pairs[0], sizeof(int2) * (size_t)cnt[0]},
+        {starts[1], h_start[1], sizeof(int) * (size_t)(P + 1)}, {pairs[1], h_pairs[1], sizeof(int2) * (size_t)cnt[1]},
+        {starts[2], h_start[2], sizeof(int) * (size_t)(P + 1)}, {pairs[2], h_pairs[2], sizeof(int2) * (size_t)cnt[2]},
+    };
+    for (const Up &u : ups)
+        if ((st = check_cuda(cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, s), "upload tables")) != FC2T2_OK)
+            return st;
+    if ((st = check_cuda(cudaMemsetAsync(pl.d_flags, 0, 4 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if (N == 0) return check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y");
+
+    // the same kernels as fc2t2_forward, on scratch-array pointers
+    if ((st = check_cuda(launch_bin_count(&pl, s, p, N, pl.src), "bin")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(&pl, s, pl.src.count, pl.src.start, pl.lev[0].G), "scan")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scatter(&pl, s, p, w, N, pl.src), "scatter")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_p2m(&pl, s, pl.src, pl.d_M), "p2m")) != FC2T2_OK) return st;
+    for (int l = 0; l + 1 < pl.nlev; ++l)
+        if ((st = check_cuda(launch_m2m(&pl, s, l), "m2m")) != FC2T2_OK) return st;
+    for (int l = pl.nlev - 1; l >= 0; --l) {
+        if ((st = check_cuda(launch_m2l(&pl, s, l), "m2l")) != FC2T2_OK) return st;
+        if (l + 1 < pl.nlev && (st = check_cuda(launch_l2l(&pl, s, l), "l2l")) != FC2T2_OK) return st;
+    }
+    if ((st = check_cuda(launch_bin_count(&pl, s, q, M, pl.qry), "bin")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(&pl, s, pl.qry.count, pl.qry.start, pl.lev[0].G), "scan")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scatter(&pl, s, q, nullptr, M, pl.qry), "scatter")) != FC2T2_OK) return st;
+    return check_cuda(launch_l2p(&pl, s, pl.qry, M, y, nullptr), "l2p");
+}
