@@ -69,10 +69,14 @@ typedef enum {
     FC2T2_KERNEL_POLY = 1
 } fc2t2_kernel;
 
+/* Arithmetic of the M2L translation, the dominant step.  The tensor-core forms apply to 3D
+ * plans; 2D plans run the CUDA-core M2L whatever is asked. */
 typedef enum {
-    FC2T2_M2L_FP32 = 0,          /* M2L in FP32 on the CUDA cores */
-    FC2T2_M2L_TF32 = 1,          /* M2L on tcgen05 tensor cores, TF32 inputs, FP32 accumulate */
-    FC2T2_M2L_BF16 = 2           /* M2L on tcgen05 tensor cores, BF16 inputs, FP32 accumulate */
+    FC2T2_M2L_FP32 = 0,          /* FP32 on the CUDA cores */
+    FC2T2_M2L_TF32 = 1,          /* tcgen05 tensor cores, TF32 operands, FP32 accumulation */
+    FC2T2_M2L_BF16 = 2,          /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
+    FC2T2_M2L_TF32X3 = 3         /* tcgen05, each operand split into TF32 high + low parts,
+                                    three products (hi*hi + hi*lo + lo*hi): FP32 accuracy */
 } fc2t2_m2l_prec;
 
 typedef struct fc2t2_plan_s *fc2t2_plan;

@@ -162,6 +162,7 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
 
     // scaled kernel derivatives per level and offset o in {-3..3}^D
     std::vector<float> dtab((size_t)pl->nlev * nofs * Pp, 0.0f);
+    std::vector<double> dtab64((size_t)pl->nlev * nofs * P, 0.0);
     std::vector<double> tmp(P);
     for (int l = 0; l < pl->nlev; ++l) {
         const double h = pl->lev[l].h;
@@ -170,7 +171,10 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
             int r = o;
             for (int d = 0; d < D; ++d) { c[d] = (double)(r % 7 - 3) * h; r /= 7; }
             scaled_derivs(pl, ix, c, h, tmp.data());
-            for (int k = 0; k < P; ++k) dtab[((size_t)l * nofs + o) * Pp + k] = (float)tmp[k];
+            for (int k = 0; k < P; ++k) {
+                dtab[((size_t)l * nofs + o) * Pp + k] = (float)tmp[k];
+                dtab64[((size_t)l * nofs + o) * P + k] = tmp[k];
+            }
         }
     }
     // child re-centring: shift[ch][g] = prod_d s_d^(g_d) / g_d!,  s_d = +1/2 (odd child) or -1/2
@@ -233,6 +237,9 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
     if ((st = upload(pl->d_l2l_pairs, l2l_pairs, "upload l2l pairs")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_m2l_start, m2l_start, "upload m2l index")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_m2l_pairs, m2l_pairs, "upload m2l pairs")) != FC2T2_OK) return st;
+    // tensor-core operator images (3D; other dimensions keep the CUDA-core M2L)
+    if (pl->desc.m2l != FC2T2_M2L_FP32 && D == 3)
+        if ((st = build_tc_operators(pl, dtab64)) != FC2T2_OK) return st;
     return FC2T2_OK;
 }
 
@@ -259,7 +266,9 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
         return set_error(FC2T2_ERR_INVALID_ARG, "unknown kernel");
     }
     if (d->channels != 1) return set_error(FC2T2_ERR_UNSUPPORTED, "only channels == 1 is supported");
-    if (d->m2l != FC2T2_M2L_FP32) return set_error(FC2T2_ERR_UNSUPPORTED, "M2L precision not available");
+    if (d->m2l != FC2T2_M2L_FP32 && d->m2l != FC2T2_M2L_TF32 && d->m2l != FC2T2_M2L_BF16 &&
+        d->m2l != FC2T2_M2L_TF32X3)
+        return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
     if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||
         d->max_queries > (int64_t)INT32_MAX)
         return set_error(FC2T2_ERR_INVALID_ARG, "max_sources / max_queries out of range");
@@ -271,13 +280,14 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
 
 static fc2t2_status finish_flags(fc2t2_plan_s *pl, cudaStream_t s) {
     if (!pl->desc.check_domain) return FC2T2_OK;
-    int flags = 0;
-    fc2t2_status st = check_cuda(cudaMemcpyAsync(&flags, pl->d_flags, sizeof(int), cudaMemcpyDeviceToHost, s),
+    int flags[2] = {0, 0};
+    fc2t2_status st = check_cuda(cudaMemcpyAsync(flags, pl->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
                                  "read flags");
     if (st != FC2T2_OK) return st;
     st = check_cuda(cudaStreamSynchronize(s), "synchronise");
     if (st != FC2T2_OK) return st;
-    if (flags & 1) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
+    if (flags[1]) return set_error(FC2T2_ERR_TIMEOUT, "a device-side wait of the tensor-core M2L gave up");
+    if (flags[0] & 1) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
     return FC2T2_OK;
 }
 
@@ -417,7 +427,7 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
     if (!q || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
     if (N == 0) {
         if ((st = check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y")) != FC2T2_OK) return st;
         if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
@@ -442,7 +452,7 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     if (!p || !w || (M > 0 && (!q || !ybar))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
     if (M == 0) {
         if (wbar && (st = check_cuda(cudaMemsetAsync(wbar, 0, sizeof(float) * N, s), "zero wbar")) != FC2T2_OK) return st;
         if (pbar && (st = check_cuda(cudaMemsetAsync(pbar, 0, sizeof(float) * N * pl->D, s), "zero pbar")) != FC2T2_OK) return st;

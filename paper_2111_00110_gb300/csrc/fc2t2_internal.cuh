@@ -106,8 +106,13 @@ struct fc2t2_plan_s {
     int64_t scan_tmp_len = 0;
     int *d_flags = nullptr;       // [4] device error flags
     fc2t2::SortWork src, qry;
-    void *d_mma_ops = nullptr;    // tensor-core M2L operators (optional)
+    void *d_mma_ops = nullptr;    // tensor-core M2L operator images (TF32 / BF16 modes)
     size_t mma_ops_bytes = 0;
+    struct TcInfo {
+        int enabled = 0, mode = 0, img_bytes = 0, ncomp = 1, pn = 0, kbytes = 0, nchunks = 0;
+        int n0[4] = {0, 0, 0, 0}, N[4] = {0, 0, 0, 0}, K[4] = {0, 0, 0, 0}, b_off[4] = {0, 0, 0, 0};
+        int nbuf = 1, nbslots = 2, smem = 0, tmem_cols = 32;
+    } tc;
 
     // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage
     mutable int64_t launches[FC2T2_NUM_STAGES] = {0, 0, 0, 0, 0, 0};
@@ -136,5 +141,7 @@ cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w);
+cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
 
 }  // namespace fc2t2

@@ -174,6 +174,7 @@ cudaError_t launch_m2l_simple(const fc2t2_plan_s *pl, cudaStream_t s, int level)
 }
 
 cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
+    if (pl->tc.enabled) return launch_m2l_tc(pl, s, level);
     return launch_m2l_simple(pl, s, level);
 }
 

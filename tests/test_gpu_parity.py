@@ -245,3 +245,33 @@ def test_uniform3d_full_size_forward_backward(lib):
     wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, ybar), sel=sel)
     assert_close(wbar[sel], wo, what="uniform3d wbar")
     assert_close(pbar[sel], po, what="uniform3d pbar")
+
+
+# ----------------------------------------------------------------- tensor-core M2L (3D)
+
+# rel-L2 bars: TF32 x 3 is FP32-accurate; single-pass TF32 / BF16 are the mixed forms
+TC_BARS = {"tf32x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2), "bf16": (1e-2, 5e-2)}
+
+
+@pytest.mark.parametrize("mode", ["tf32x3", "tf32", "bf16"])
+@pytest.mark.parametrize("grid,order", [(16, 4), (16, 6), (32, 6), (8, 3)])
+def test_tensor_core_m2l_forward(lib, mode, grid, order):
+    wl = workloads.uniform(500 + grid + order, 3, 6000, 5000, grid, order, 1.3 / grid)
+    plan = make_plan(3, grid, order, wl.sigma, wl.N, wl.M, m2l=mode)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    yo = oracle.forward(odesc(3, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    rel, elem = TC_BARS[mode]
+    print(f"{mode} n{grid} rho{order}: rel-L2 {rel_l2(y, yo):.3e}")
+    assert_close(y, yo, rel=rel, elem=elem, what=f"{mode} n{grid} rho{order}")
+
+
+@pytest.mark.parametrize("mode", ["tf32x3", "tf32"])
+def test_tensor_core_m2l_backward(lib, mode):
+    wl = workloads.uniform(777, 3, 4000, 3500, 16, 6, 0.08)
+    ybar = wl.ybar()
+    plan = make_plan(3, 16, 6, wl.sigma, wl.N, wl.M, m2l=mode)
+    wbar, pbar = run_backward(plan, wl.p, wl.w, wl.q, ybar)
+    wo, po = oracle.backward(odesc(3, 16, 6, wl.sigma), *f64(wl.p, wl.w, wl.q, ybar))
+    rel, elem = TC_BARS[mode]
+    assert_close(wbar, wo, rel=rel, elem=elem, what=f"{mode} wbar")
+    assert_close(pbar, po, rel=rel, elem=elem, what=f"{mode} pbar")
