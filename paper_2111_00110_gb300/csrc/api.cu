@@ -150,6 +150,7 @@ static void destroy(fc2t2_plan_s *pl) {
     cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
     cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
     cudaFree(pl->d_mma_ops);
+    for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
     free_sort(pl->src);
     free_sort(pl->qry);
     delete pl;
@@ -216,6 +217,8 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
     }
     m2m_start[P] = (int)m2m_pairs.size();
     l2l_start[P] = (int)l2l_pairs.size();
+    pl->n_m2m_pairs = (int)m2m_pairs.size();
+    pl->n_l2l_pairs = (int)l2l_pairs.size();
     m2l_start[P] = (int)m2l_pairs.size();
 
     fc2t2_status st;

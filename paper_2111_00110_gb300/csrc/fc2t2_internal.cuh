@@ -98,8 +98,10 @@ struct fc2t2_plan_s {
     float *d_pow2 = nullptr;      // [P]  2^-|a|
     int *d_m2m_start = nullptr;   // [P+1]  per a: pairs (b, a-b) with b <= a
     int2 *d_m2m_pairs = nullptr;
+    int n_m2m_pairs = 0;
     int *d_l2l_start = nullptr;   // [P+1]  per k: pairs (g, g-k) with g >= k
     int2 *d_l2l_pairs = nullptr;
+    int n_l2l_pairs = 0;
     int *d_m2l_start = nullptr;   // [P+1]  per k: pairs (b, k+b) with |b| <= rho-|k|
     int2 *d_m2l_pairs = nullptr;
     int *d_scan_tmp = nullptr;    // block sums of the prefix scan
@@ -112,6 +114,10 @@ struct fc2t2_plan_s {
         int enabled = 0, mode = 0, img_bytes = 0, ncomp = 1, pn = 0, kbytes = 0, nchunks = 0;
         int n0[4] = {0, 0, 0, 0}, N[4] = {0, 0, 0, 0}, K[4] = {0, 0, 0, 0}, b_off[4] = {0, 0, 0, 0};
         int nbuf = 1, nbslots = 2, smem = 0, tmem_cols = 32;
+        double mma_flops = 0.0;                       // tensor-core work issued per transform
+        void *packed[fc2t2::kMaxLevels] = {};         // moments in the tensor-core layout, per level
+        int level_ok[fc2t2::kMaxLevels] = {};         // 1: this level runs on the tensor cores
+        alignas(64) unsigned char maps[fc2t2::kMaxLevels][2][128] = {};   // TMA descriptors (hi, lo)
     } tc;
 
     // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage

@@ -6,19 +6,30 @@
 //     Lt[a, k] += sum_b  Mt_sigma[a + delta, b] * B_o[k, b],   B_o[k, b] = (-1)^|k| Dt_o[k+b]
 // (|k| + |b| <= rho), with a the target's index in the half-resolution sub-grid.  A CTA owns
 // 128 targets (8 x 16 sub-grid cells in x, y at one z) of one class: its accumulator is a
-// 128 x Pn FP32 tile in tensor memory.  For each (sigma, delta_z) the CTA stages the 10 x 18
-// cell "slab" of sub-grid sigma around its tile (converted to BF16 or TF32) in shared memory;
-// the nine (delta_x, delta_y) operands are views of that slab that differ only in their start
-// address.  The operators B_o are precomputed per level in the shared-memory image and fetched
-// with bulk copies.  Because |k| + |b| <= rho, the k range is cut into chunks that only run
-// over the b range they can reach (degree-block skipping), e.g. rho = 6: k in [0,16) x b < 96,
-// [16,32) x b < 32, [32,96) x b < 16 -- 3072 of 9216 dense multiply-adds.
+// 128 x Pn FP32 tile in tensor memory.
+//
+// Operands.  A pack kernel rewrites each level's moments once into the tensor-core layout:
+// per source parity sigma and sub-grid z, 16-byte chunks of 8 BF16 (or 4 TF32) coefficients
+// ordered [chunk][y][x] -- exactly the canonical no-swizzle K-major layout, so one TMA tensor
+// load brings the 10 x 18 cell "slab" of sub-grid sigma around the tile into shared memory
+// (cells outside the grid arrive as zeros).  The nine (delta_x, delta_y) A operands of a slab
+// are views that differ only in their start address.  The operators B_o are precomputed per
+// level as shared-memory images and fetched with bulk copies.  Because |k| + |b| <= rho, the
+// k range is cut into chunks that only run over the b range they can reach (degree-block
+// skipping), e.g. rho = 6: k in [0,16) x b < 96, [16,32) x b < 32, [32,96) x b < 16 -- 3072 of
+// 9216 dense multiply-adds.
 //
 // Precision: BF16 or TF32 operands with FP32 accumulation, or TF32 x 3 (A_hi B_hi + A_hi B_lo
-// + A_lo B_hi, the low parts being the TF32 rounding residues) which is accurate to FP32.
+// + A_lo B_hi, the low parts being the TF32 rounding residues), accurate to FP32.  The tensor
+// core's accumulation over thousands of MMAs loses low bits, so each step's partial sum is
+// accumulated in its own TMEM buffer (two, alternating) and added into FP32 registers.
 //
-// Warp roles: warp 0 lane 0 issues bulk copies and MMAs; warps 1-4 stage slabs and, at the end,
-// read the accumulator (each warp reads its TMEM lane quarter) and write Lt rows.
+// Warp roles: warp 0 lane 0 fetches slabs (TMA) and operators (bulk copies), warp 1 lane 0
+// issues the MMAs, warps 2-5 add each step's partial accumulator into FP32 registers (each
+// warp reads its TMEM lane quarter) and finally write the Lt rows.  Every wait is bounded.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cstring>
 #include <vector>
 
@@ -29,10 +40,11 @@ namespace fc2t2 {
 
 using namespace tc;
 
-constexpr int kTcThreads = 160;
+constexpr int kTcThreads = 192;
 constexpr int kSlabCells = 180;          // 10 x 18 cells
 constexpr int kMaxChunks = 4;
 constexpr int kMaxBSlots = 8;
+constexpr int kMaxSlabSlots = 3;
 
 struct TcChunk {
     int n0, N, K;     // k columns [n0, n0 + N), b range [0, K)
@@ -40,22 +52,21 @@ struct TcChunk {
 };
 
 struct TcArgs {
-    const float *M;               // level coefficients [G][Pp]
     float *L;
     const unsigned char *B;       // operator images of this level: [343][ncomp][img_bytes]
     int *err;
     int nl;                       // cells per dimension at this level
     int Pp;
     int finest;                   // 1: no hole
-    int kbytes;                   // bytes per slab row (covers the largest chunk K)
+    int nkc;                      // 16-byte chunks per slab row
     int img_bytes;                // one operator image (one component)
     int ncomp_b;                  // 1, or 2 for TF32 x 3 (hi, lo)
     int nchunks;
     TcChunk ch[kMaxChunks];
     int pn;                       // accumulator columns used
     uint32_t tmem_cols;
-    int nslab_buf;                // 1 or 2
-    int nbslots;
+    int nslab;                    // slab ring slots
+    int nbslots;                  // operator ring slots
     int tiles_x, tiles_y;         // tiles per parity class along x, y (z: half)
 };
 
@@ -64,21 +75,78 @@ struct TcMode {
     static constexpr int esz = MODE == 0 ? 2 : 4;
     static constexpr int epc = 16 / esz;          // elements per 16-byte chunk
     static constexpr int eps = 32 / esz;          // elements per MMA K-step
-    static constexpr int ncomp_a = MODE == 2 ? 2 : 1;
+    static constexpr int ncomp = MODE == 2 ? 2 : 1;
     static constexpr uint32_t fmt = MODE == 0 ? 1u : 2u;
 };
 
+__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            int c4, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+        "%6}], [%7];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------------------------ pack
+// Mtc[comp][sigma][z + 1][kc][y][x] (16 bytes each) from Mt[cell][Pp]; z planes -1 and half
+// stay zero.  comp 1 (TF32 x 3) holds the TF32 rounding residue of comp 0.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_pack_tc(const float *__restrict__ M, unsigned char *__restrict__ out,
+                                                 int nl, int Pp, int nkc) {
+    using Md = TcMode<MODE>;
+    const int half = nl >> 1;
+    const int64_t plane = (int64_t)nkc * half * half;          // chunks per (sigma, z)
+    const int64_t total = (int64_t)8 * half * plane;
+    const int64_t comp_stride = (int64_t)8 * (half + 2) * plane * 16;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        int64_t r = i;
+        const int x = (int)(r % half); r /= half;
+        const int y = (int)(r % half); r /= half;
+        const int kc = (int)(r % nkc); r /= nkc;
+        const int z = (int)(r % half);
+        const int sg = (int)(r / half);
+        const int64_t cell = (int64_t)(2 * x + (sg & 1)) +
+                             (int64_t)nl * ((2 * y + ((sg >> 1) & 1)) + (int64_t)nl * (2 * z + (sg >> 2)));
+        const float *row = M + cell * Pp;
+        const int k0 = kc * Md::epc;
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#pragma unroll
+        for (int q4 = 0; q4 < Md::epc / 4; ++q4)
+            if (k0 + 4 * q4 + 4 <= Pp) {
+                const float4 f = __ldg(reinterpret_cast<const float4 *>(row + k0 + 4 * q4));
+                v[4 * q4] = f.x; v[4 * q4 + 1] = f.y; v[4 * q4 + 2] = f.z; v[4 * q4 + 3] = f.w;
+            }
+        const int64_t o = ((((int64_t)sg * (half + 2) + (z + 1)) * nkc + kc) * half + y) * half + x;
+        uint4 *dst = reinterpret_cast<uint4 *>(out + o * 16);
+        if (MODE == 0) {
+            *dst = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                              pack_bf16x2(v[6], v[7]));
+        } else {
+            float h[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) h[e] = round_tf32(v[e]);
+            *dst = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]), __float_as_uint(h[2]), __float_as_uint(h[3]));
+            if (MODE == 2)
+                *reinterpret_cast<uint4 *>(out + comp_stride + o * 16) =
+                    make_uint4(__float_as_uint(round_tf32(v[0] - h[0])), __float_as_uint(round_tf32(v[1] - h[1])),
+                               __float_as_uint(round_tf32(v[2] - h[2])), __float_as_uint(round_tf32(v[3] - h[3])));
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------ M2L
 template <int MODE, int PNMAX>
-__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs args) {
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_m2l_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcArgs args) {
     using Md = TcMode<MODE>;
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t bar_bfull[kMaxBSlots], bar_bfree[kMaxBSlots], bar_sfull[2], bar_sfree[2];
+    __shared__ uint64_t bar_bfull[kMaxBSlots], bar_bfree[kMaxBSlots], bar_sfull[kMaxSlabSlots], bar_sfree[kMaxSlabSlots];
     __shared__ uint64_t bar_accfull[2], bar_accfree[2], bar_done;
     __shared__ uint32_t tmem_base;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = args.nl >> 1;
-    // block -> (parity class, tile)
     const int tiles_per_class = args.tiles_x * args.tiles_y * half;
     const int pi = blockIdx.x / tiles_per_class;
     int tr = blockIdx.x % tiles_per_class;
@@ -89,20 +157,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs args) {
     const int ax0 = tx * 8, ay0 = ty * 16;
     const int pix = pi & 1, piy = (pi >> 1) & 1, piz = (pi >> 2) & 1;
 
-    const int slab_bytes = kSlabCells * args.kbytes;             // one component
-    const int slab_stride = slab_bytes * Md::ncomp_a;            // one buffer
+    const int box_bytes = kSlabCells * 16 * args.nkc;           // bytes one TMA slab load delivers
+    const int slab_bytes = (box_bytes + 1023) & ~1023;          // one component, 1024-aligned
+    const int slab_stride = slab_bytes * Md::ncomp;              // one ring slot
     unsigned char *slabs = smem;
-    unsigned char *bring = smem + ((args.nslab_buf * slab_stride + 1023) & ~1023);
+    unsigned char *bring = smem + ((args.nslab * slab_stride + 1023) & ~1023);
     const int bslot_bytes = args.img_bytes * args.ncomp_b;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < args.nbslots; ++i) { mbar_init(&bar_bfull[i], 1); mbar_init(&bar_bfree[i], 1); }
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(&bar_sfull[i], 128);
-            mbar_init(&bar_sfree[i], 1);
-            mbar_init(&bar_accfull[i], 1);
-            mbar_init(&bar_accfree[i], 128);
-        }
+        for (int i = 0; i < args.nslab; ++i) { mbar_init(&bar_sfull[i], 1); mbar_init(&bar_sfree[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&bar_accfull[i], 1); mbar_init(&bar_accfree[i], 128); }
         mbar_init(&bar_done, 1);
     }
     fence_proxy_async_smem();
@@ -113,112 +178,118 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs args) {
     const uint32_t tacc = tmem_base;
 
     bool ok = true;
+    int c_n0[kMaxChunks], c_N[kMaxChunks], c_K[kMaxChunks], c_boff[kMaxChunks];
+#pragma unroll
+    for (int c = 0; c < kMaxChunks; ++c) {
+        c_n0[c] = args.ch[c].n0; c_N[c] = args.ch[c].N; c_K[c] = args.ch[c].K; c_boff[c] = args.ch[c].b_off;
+    }
+    // operators of step s = (sigma, dz), then (dx, dy); the hole is skipped above the finest level
+    auto op_of = [&](int s, int dx, int dy, int &olin) -> bool {
+        const int sg = s / 3, dz = s % 3 - 1;
+        const int ox = 2 * dx + (sg & 1) - pix, oy = 2 * dy + ((sg >> 1) & 1) - piy, oz = 2 * dz + (sg >> 2) - piz;
+        if (!args.finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return false;
+        olin = (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);
+        return true;
+    };
     if (warp == 0) {
         if (lane == 0) {
-            // ---------------------------------------------------------------- issuer
-            // operators in consumption order: step s = (sigma, dz), within a step (dx, dy);
-            // above the finest level the 3^D hole is skipped
-            int seq_o[216];
-            unsigned char seq_step[216];
-            int nseq = 0;
-            for (int s = 0; s < 24; ++s) {
-                const int sg = s / 3, dz = s % 3 - 1;
-                const int sx = sg & 1, sy = (sg >> 1) & 1, sz = sg >> 2;
-                for (int dy = -1; dy <= 1; ++dy)
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int ox = 2 * dx + sx - pix, oy = 2 * dy + sy - piy, oz = 2 * dz + sz - piz;
-                        const bool hole = !args.finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 &&
-                                          oz <= 1;
-                        if (hole) continue;
-                        seq_o[nseq] = ((ox + 3) + 7 * (oy + 3) + 49 * (oz + 3)) | ((dx + 1) << 16) | ((dy + 1) << 20);
-                        seq_step[nseq] = (unsigned char)s;
-                        ++nseq;
-                    }
-            }
-            int issued = 0;
-            auto load_b = [&](int j) {
-                issued = j + 1;
-                const int slot = j % args.nbslots;
-                const int olin = seq_o[j] & 0xFFFF;
-                mbar_arrive_expect_tx(&bar_bfull[slot], (uint32_t)bslot_bytes);
-                bulk_g2s(bring + slot * bslot_bytes, args.B + (size_t)olin * bslot_bytes, (uint32_t)bslot_bytes,
-                         &bar_bfull[slot]);
-            };
-            const int pre = nseq < args.nbslots ? nseq : args.nbslots;
-            for (int j = 0; j < pre; ++j) load_b(j);
-            const uint32_t lboA = kSlabCells * 16, sboA = 160;
+            // ---------------------------------------------------------------- producer
             int j = 0;
             for (int s = 0; s < 24 && ok; ++s) {
-                const int buf = s % args.nslab_buf;
-                const int use = s / args.nslab_buf;    // earlier fills of this slab buffer
-                const int ab = s & 1;                  // accumulator buffer of this step
+                const int slot = s % args.nslab, use = s / args.nslab;
+                if (use >= 1 && !mbar_wait(&bar_sfree[slot], (use - 1) & 1, args.err, 16)) { ok = false; break; }
+                const int sg = s / 3, dz = s % 3 - 1;
+                mbar_arrive_expect_tx(&bar_sfull[slot], (uint32_t)(box_bytes * Md::ncomp));
+                unsigned char *dst = slabs + slot * slab_stride;
+                // z plane index includes the zero plane below z = 0
+                const int zc = sg * (half + 2) + (az + dz + 1);
+                tma_load_5d(dst, &map_hi, 0, ax0 - 1, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                if (MODE == 2) tma_load_5d(dst + slab_bytes, &map_lo, 0, ax0 - 1, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                for (int t9 = 0; t9 < 9 && ok; ++t9) {
+                    int olin;
+                    if (!op_of(s, t9 % 3 - 1, t9 / 3 - 1, olin)) continue;
+                    const int bslot = j % args.nbslots, buse = j / args.nbslots;
+                    if (buse >= 1 && !mbar_wait(&bar_bfree[bslot], (buse - 1) & 1, args.err, 16)) { ok = false; break; }
+                    mbar_arrive_expect_tx(&bar_bfull[bslot], (uint32_t)bslot_bytes);
+                    bulk_g2s(bring + bslot * bslot_bytes, args.B + (size_t)olin * bslot_bytes, (uint32_t)bslot_bytes,
+                             &bar_bfull[bslot]);
+                    ++j;
+                }
+            }
+            // bounded drain of the last copies of every ring slot
+            for (int jj = (j - args.nbslots > 0 ? j - args.nbslots : 0); jj < j; ++jj)
+                mbar_wait(&bar_bfull[jj % args.nbslots], (jj / args.nbslots) & 1, args.err, 128);
+            for (int s = 24 - args.nslab; s < 24; ++s)
+                mbar_wait(&bar_sfull[s % args.nslab], (s / args.nslab) & 1, args.err, 128);
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------------------- MMA issuer
+            const uint32_t lboA = kSlabCells * 16, sboA = 160;
+            const uint64_t a_step = (uint64_t)((2u * lboA) >> 4);      // descriptor increment per K-step
+            int j = 0;
+            for (int s = 0; s < 24 && ok; ++s) {
+                const int slot = s % args.nslab, use = s / args.nslab;
+                const int ab = s & 1;
                 if (s >= 2 && !mbar_wait(&bar_accfree[ab], ((s - 2) >> 1) & 1, args.err, 4)) { ok = false; break; }
-                if (!mbar_wait(&bar_sfull[buf], use & 1, args.err, 4)) { ok = false; break; }
+                if (!mbar_wait(&bar_sfull[slot], use & 1, args.err, 4)) { ok = false; break; }
                 tc_fence_after();
-                const uint32_t slab_a = smem_u32(slabs + buf * slab_stride);
+                const uint32_t slab_a = smem_u32(slabs + slot * slab_stride);
                 const uint32_t acc_col = tacc + (uint32_t)(ab * args.pn);
-                uint32_t started = 0;                  // bit c: chunk c written in this step
-                for (; j < nseq && seq_step[j] == s; ++j) {
-                    const int slot = j % args.nbslots;
-                    if (!mbar_wait(&bar_bfull[slot], (j / args.nbslots) & 1, args.err, 8)) { ok = false; break; }
+                uint32_t started = 0;
+                for (int t9 = 0; t9 < 9; ++t9) {
+                    int olin;
+                    const int dx = t9 % 3 - 1, dy = t9 / 3 - 1;
+                    if (!op_of(s, dx, dy, olin)) continue;
+                    const int bslot = j % args.nbslots;
+                    if (!mbar_wait(&bar_bfull[bslot], (j / args.nbslots) & 1, args.err, 8)) { ok = false; break; }
                     tc_fence_after();
-                    const int dx = ((seq_o[j] >> 16) & 0xF) - 1, dy = ((seq_o[j] >> 20) & 0xF) - 1;
-                    const uint32_t b_img = smem_u32(bring + slot * bslot_bytes);
+                    const uint32_t b_img = smem_u32(bring + bslot * bslot_bytes);
                     const uint32_t a_view = slab_a + (uint32_t)(((dy + 1) * 10 + (dx + 1)) * 16);
-                    for (int c = 0; c < args.nchunks; ++c) {
-                        const TcChunk &chk = args.ch[c];
-                        const uint32_t lboB = (uint32_t)(chk.N / 8) * 128u;
-                        const uint32_t idesc = instr_desc(Md::fmt, (uint32_t)chk.N);
-                        const uint32_t dcol = acc_col + (uint32_t)chk.n0;
-                        const int nks = chk.K / Md::eps;
-                        // passes: (A_hi, B_hi); for TF32 x 3 also (A_hi, B_lo), (A_lo, B_hi)
+#pragma unroll
+                    for (int c = 0; c < kMaxChunks; ++c) {
+                        if (c >= args.nchunks) break;
+                        const uint32_t lboB = (uint32_t)(c_N[c] / 8) * 128u;
+                        const uint64_t b_step = (uint64_t)((2u * lboB) >> 4);
+                        const uint32_t idesc = instr_desc(Md::fmt, (uint32_t)c_N[c]);
+                        const uint32_t dcol = acc_col + (uint32_t)c_n0[c];
+                        const int nks = c_K[c] / Md::eps;
+#pragma unroll
                         for (int pass = 0; pass < (MODE == 2 ? 3 : 1); ++pass) {
-                            const uint32_t abase = a_view + (pass == 2 ? (uint32_t)slab_bytes : 0u);
-                            const uint32_t bbase =
-                                b_img + (uint32_t)chk.b_off + (pass == 1 ? (uint32_t)args.img_bytes : 0u);
+                            uint64_t ad = smem_desc(a_view + (pass == 2 ? (uint32_t)slab_bytes : 0u), lboA, sboA);
+                            uint64_t bd = smem_desc(b_img + (uint32_t)c_boff[c] + (pass == 1 ? (uint32_t)args.img_bytes : 0u),
+                                                    lboB, 128u);
+                            uint32_t accum = (started >> c) & 1u;
                             for (int ks = 0; ks < nks; ++ks) {
-                                const uint64_t ad = smem_desc(abase + (uint32_t)ks * 2u * lboA, lboA, sboA);
-                                const uint64_t bd = smem_desc(bbase + (uint32_t)ks * 2u * lboB, lboB, 128u);
-                                const uint32_t accum = (started >> c) & 1u;
                                 if (MODE == 0) mma_bf16(dcol, ad, bd, idesc, accum);
                                 else mma_tf32(dcol, ad, bd, idesc, accum);
-                                started |= 1u << c;
+                                ad += a_step;
+                                bd += b_step;
+                                accum = 1u;
                             }
+                            started |= 1u << c;
                         }
                     }
-                    mma_commit(&bar_bfree[slot]);
-                    // refill the previous operator's slot once its MMAs have completed
-                    if (j >= 1) {
-                        const int jp = j - 1 + args.nbslots;
-                        if (jp < nseq && jp >= args.nbslots) {
-                            const int ps = (j - 1) % args.nbslots;
-                            if (!mbar_wait(&bar_bfree[ps], ((j - 1) / args.nbslots) & 1, args.err, 16)) { ok = false; break; }
-                            load_b(jp);
-                        }
-                    }
+                    mma_commit(&bar_bfree[bslot]);
+                    ++j;
                 }
                 if (!ok) break;
-                mma_commit(&bar_sfree[buf]);
+                mma_commit(&bar_sfree[slot]);
                 mma_commit(&bar_accfull[ab]);
             }
             mma_commit(&bar_done);
-            // after an error, wait (bounded) for operator copies still in flight
-            for (int jj = j; jj < issued; ++jj)
-                mbar_wait(&bar_bfull[jj % args.nbslots], (jj / args.nbslots) & 1, args.err, 128);
         }
         __syncwarp();
     } else {
-        // ---------------------------------------------------------------- stagers / epilogue
-        const int ts = threadIdx.x - 32;
-        const int nkc = args.kbytes / 16;
+        // ---------------------------------------------------------------- accumulate / write
         const int q = warp & 3;                 // TMEM lane quarter of this warp
         float acc[PNMAX];
 #pragma unroll
         for (int i = 0; i < PNMAX; ++i) acc[i] = 0.0f;
-        // add the partial sums of step u (accumulator buffer u & 1) into FP32 registers
-        auto flush = [&](int u) {
+        for (int u = 0; u < 24 && ok; ++u) {
             const int ab = u & 1;
-            if (!mbar_wait(&bar_accfull[ab], (u >> 1) & 1, args.err, 32)) { ok = false; return; }
+            if (!mbar_wait(&bar_accfull[ab], (u >> 1) & 1, args.err, 32)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll
             for (int c0 = 0; c0 < PNMAX; c0 += 16) {
@@ -231,55 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const TcArgs args) {
             }
             tc_fence_before();
             mbar_arrive(&bar_accfree[ab]);
-        };
-        for (int s = 0; s < 24 && ok; ++s) {
-            const int buf = s % args.nslab_buf;
-            const int use = s / args.nslab_buf;
-            if (use >= 1 && !mbar_wait(&bar_sfree[buf], (use - 1) & 1, args.err, 32)) { ok = false; break; }
-            const int sg = s / 3, dz = s % 3 - 1;
-            const int sx = sg & 1, sy = (sg >> 1) & 1, sz = sg >> 2;
-            unsigned char *dst = slabs + buf * slab_stride;
-            const int cz = az + dz;
-            for (int idx = ts; idx < nkc * kSlabCells; idx += 128) {
-                const int cell = idx % kSlabCells, kc = idx / kSlabCells;
-                const int cx = ax0 - 1 + cell % 10, cy = ay0 - 1 + cell / 10;
-                const bool in = cx >= 0 && cx < half && cy >= 0 && cy < half && cz >= 0 && cz < half;
-                const int k0 = kc * Md::epc;
-                float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-                if (in) {
-                    const int64_t lin = (int64_t)(2 * cx + sx) +
-                                        (int64_t)args.nl * ((2 * cy + sy) + (int64_t)args.nl * (2 * cz + sz));
-                    const float *row = args.M + lin * args.Pp;
-#pragma unroll
-                    for (int q4 = 0; q4 < Md::epc / 4; ++q4) {
-                        if (k0 + 4 * q4 + 4 <= args.Pp) {
-                            const float4 f = __ldg(reinterpret_cast<const float4 *>(row + k0 + 4 * q4));
-                            v[4 * q4] = f.x; v[4 * q4 + 1] = f.y; v[4 * q4 + 2] = f.z; v[4 * q4 + 3] = f.w;
-                        }
-                    }
-                }
-                unsigned char *d16 = dst + ((size_t)kc * kSlabCells + cell) * 16;
-                if (MODE == 0) {
-                    *reinterpret_cast<uint4 *>(d16) = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
-                                                                 pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
-                } else {
-                    float h[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) h[e] = round_tf32(v[e]);
-                    *reinterpret_cast<uint4 *>(d16) = make_uint4(__float_as_uint(h[0]), __float_as_uint(h[1]),
-                                                                 __float_as_uint(h[2]), __float_as_uint(h[3]));
-                    if (MODE == 2)
-                        *reinterpret_cast<uint4 *>(d16 + slab_bytes) = make_uint4(
-                            __float_as_uint(round_tf32(v[0] - h[0])), __float_as_uint(round_tf32(v[1] - h[1])),
-                            __float_as_uint(round_tf32(v[2] - h[2])), __float_as_uint(round_tf32(v[3] - h[3])));
-                }
-            }
-            fence_proxy_async_smem();
-            mbar_arrive(&bar_sfull[buf]);
-            if (s >= 1) flush(s - 1);
         }
-        if (ok) flush(23);
-        // ---------------------------------------------------------------- write Lt rows
         if (ok) {
             const int r = q * 32 + lane;            // tile row
             const int x = ax0 + (r & 7), y = ay0 + (r >> 3);
@@ -322,7 +345,6 @@ void plan_chunks(int D, int rho, int P, int kg, std::vector<TcChunk> &out, int &
         const int cnt = ncoef(D, rho - d);
         return (cnt + kg - 1) / kg * kg;
     };
-    // dp[i][c]: best cost covering blocks [i, nb) with c chunks left
     const long INF = 1L << 60;
     std::vector<std::vector<long>> dp(nb + 1, std::vector<long>(kMaxChunks + 1, INF));
     std::vector<std::vector<int>> nxt(nb + 1, std::vector<int>(kMaxChunks + 1, -1));
@@ -356,7 +378,7 @@ uint16_t to_bf16(float x) {
     u += 0x7FFFu + ((u >> 16) & 1u);
     return (uint16_t)(u >> 16);
 }
-float to_tf32(float x) {   // round half away from zero on the 13 dropped bits (cvt.rna)
+float to_tf32(float x) {   // round half away from zero on the 13 dropped bits (as cvt.rna)
     uint32_t u;
     std::memcpy(&u, &x, 4);
     u += 0x1000u;
@@ -366,27 +388,60 @@ float to_tf32(float x) {   // round half away from zero on the 13 dropped bits (
     return r;
 }
 
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
 }  // namespace
 
-// Build the tensor-core operator images of every level from the FP32/FP64 derivative table.
+// Build the tensor-core operator images of every level from the FP64 derivative table,
+// the packed-moment buffers and their TMA descriptors.
 fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
     pl->tc.enabled = 0;
     if (pl->D != 3) return FC2T2_OK;
     const int mode = pl->desc.m2l == FC2T2_M2L_BF16 ? 0 : (pl->desc.m2l == FC2T2_M2L_TF32 ? 1 : 2);
-    // a bounded issuer: remember in-flight operator loads to drain them on an error
     const int esz = mode == 0 ? 2 : 4, epc = 16 / esz, kg = 32 / esz;
     std::vector<TcChunk> ch;
     int pn = 0, kfull = 0;
     plan_chunks(pl->D, pl->rho, pl->P, kg, ch, pn, kfull);
+    if (pn > 176) return FC2T2_OK;
     int off = 0;
     for (auto &c : ch) { c.b_off = off; off += c.N * c.K * esz; }
     const int img = off;
     const int ncomp = mode == 2 ? 2 : 1;
     const int nofs = 343;
-    // degree of every graded index
+    const int nkc = kfull * esz / 16;
+    // shared memory: slab ring + operator ring (two CTAs per SM when both fit in half of it)
+    const int slab = ((kSlabCells * 16 * nkc + 1023) & ~1023) * ncomp;   // as in the kernel
+    const int bslot = img * ncomp;
+    int nslab = 0, nbs = 0, smem = 0;
+    for (int budget : {112 * 1024, 220 * 1024}) {
+        for (int ns = kMaxSlabSlots; ns >= 1 && !nslab; --ns) {
+            if (ns < 2 && budget <= 112 * 1024) continue;
+            for (int nb = kMaxBSlots; nb >= 3; --nb) {
+                const int bytes = ((ns * slab + 1023) & ~1023) + nb * bslot;
+                if (bytes <= budget) { nslab = ns; nbs = nb; smem = bytes; break; }
+            }
+        }
+        if (nslab) break;
+    }
+    if (!nslab) return FC2T2_OK;   // too large for shared memory: the CUDA-core M2L runs instead
+    PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
+    if (!enc) return FC2T2_OK;
+
     std::vector<int> deg(pl->P);
     for (int k = 0; k < pl->P; ++k) deg[k] = degree_of(pl->D, k);
-    // graded index of k + b: via exponents
     std::vector<int> ex(3 * pl->P);
     for (int a0 = 0; a0 <= pl->rho; ++a0)
         for (int a1 = 0; a0 + a1 <= pl->rho; ++a1)
@@ -433,7 +488,34 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     pl->mma_ops_bytes = host.size();
     if ((e = cudaMemcpy(pl->d_mma_ops, host.data(), host.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
         return check_cuda(e, "upload tensor-core operators");
-    // remember the layout
+
+    // packed moments per level: [comp][sigma][half + 2][nkc][half][half] x 16 bytes, zeroed once
+    for (int l = 0; l < pl->nlev; ++l) {
+        const int half = pl->lev[l].n >> 1;
+        const size_t comp_bytes = (size_t)8 * (half + 2) * nkc * half * half * 16;
+        void *buf = nullptr;
+        if ((e = cudaMalloc(&buf, comp_bytes * ncomp)) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(FC2T2_ERR_OOM, "cudaMalloc failed for packed moments");
+        }
+        pl->tc.packed[l] = buf;
+        pl->tc.level_ok[l] = 1;
+        if ((e = cudaMemset(buf, 0, comp_bytes * ncomp)) != cudaSuccess) return check_cuda(e, "clear packed moments");
+        for (int comp = 0; comp < ncomp; ++comp) {
+            cuuint64_t dims[5] = {16, (cuuint64_t)half, (cuuint64_t)half, (cuuint64_t)nkc, (cuuint64_t)8 * (half + 2)};
+            cuuint64_t strides[4] = {16, (cuuint64_t)16 * half, (cuuint64_t)16 * half * half,
+                                     (cuuint64_t)16 * half * half * nkc};
+            cuuint32_t box[5] = {16, 10, 18, (cuuint32_t)nkc, 1};
+            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+            CUresult r = enc(reinterpret_cast<CUtensorMap *>(&pl->tc.maps[l][comp]), CU_TENSOR_MAP_DATA_TYPE_UINT8, 5,
+                             static_cast<unsigned char *>(buf) + comp * comp_bytes, dims, strides, box, estr,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            // a level whose grid the descriptor cannot describe keeps the CUDA-core M2L
+            if (r != CUDA_SUCCESS) pl->tc.level_ok[l] = 0;
+        }
+        if (ncomp == 1) std::memcpy(&pl->tc.maps[l][1], &pl->tc.maps[l][0], sizeof(pl->tc.maps[l][0]));
+    }
     pl->tc.mode = mode;
     pl->tc.img_bytes = img;
     pl->tc.ncomp = ncomp;
@@ -443,33 +525,51 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     for (size_t i = 0; i < ch.size(); ++i) {
         pl->tc.n0[i] = ch[i].n0; pl->tc.N[i] = ch[i].N; pl->tc.K[i] = ch[i].K; pl->tc.b_off[i] = ch[i].b_off;
     }
-    // shared memory: slab buffers + operator ring
-    const int ncomp_a = mode == 2 ? 2 : 1;
-    const int slab = kSlabCells * pl->tc.kbytes * ncomp_a;
-    const int bslot = img * ncomp;
-    int best = -1;
-    for (int nbuf = 2; nbuf >= 1 && best < 0; --nbuf)
-        for (int nbs = kMaxBSlots; nbs >= 2; --nbs) {
-            const size_t bytes = (size_t)((nbuf * slab + 1023) & ~1023) + (size_t)nbs * bslot;
-            if (bytes <= 200 * 1024) { pl->tc.nbuf = nbuf; pl->tc.nbslots = nbs; pl->tc.smem = (int)bytes; best = 1; break; }
-        }
-    pl->tc.enabled = (best > 0 && pl->D == 3 && pn <= 256) ? 1 : 0;
+    pl->tc.nbuf = nslab;
+    pl->tc.nbslots = nbs;
+    pl->tc.smem = smem;
     const int cols = 2 * pn;   // two accumulator buffers
     pl->tc.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
+    // MMA work issued per transform (2 x multiply-adds), for roofline reporting
+    double per_op = 0.0;
+    for (const TcChunk &c : ch) per_op += 2.0 * 128 * c.N * c.K * (mode == 2 ? 3 : 1);
+    double total = 0.0;
+    for (int l = 0; l < pl->nlev; ++l) {
+        const int half = pl->lev[l].n >> 1;
+        const double tiles = 8.0 * ((half + 7) / 8) * ((half + 15) / 16) * half;
+        total += tiles * (l == 0 ? 216 : 189) * per_op;
+    }
+    pl->tc.mma_flops = total;
+    pl->tc.enabled = 1;
     return FC2T2_OK;
 }
 
 cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     const Level &lv = pl->lev[level];
+    const int half = lv.n >> 1;
+    const int nkc = pl->tc.kbytes / 16;
+    // pack this level's moments into the tensor-core layout
+    {
+        const int64_t total = (int64_t)8 * half * half * half * nkc;
+        const int64_t want = (total + 255) / 256;
+        const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+        const float *M = pl->d_M + lv.off * pl->Pp;
+        unsigned char *out = static_cast<unsigned char *>(pl->tc.packed[level]);
+        pl->launches[FC2T2_STAGE_M2L] += 1;
+        if (pl->tc.mode == 0) k_pack_tc<0><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+        else if (pl->tc.mode == 1) k_pack_tc<1><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+        else k_pack_tc<2><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     TcArgs a;
-    a.M = pl->d_M + lv.off * pl->Pp;
     a.L = pl->d_L + lv.off * pl->Pp;
     a.B = static_cast<const unsigned char *>(pl->d_mma_ops) + (size_t)level * 343 * pl->tc.ncomp * pl->tc.img_bytes;
     a.err = pl->d_flags + 1;
     a.nl = lv.n;
     a.Pp = pl->Pp;
     a.finest = level == 0 ? 1 : 0;
-    a.kbytes = pl->tc.kbytes;
+    a.nkc = nkc;
     a.img_bytes = pl->tc.img_bytes;
     a.ncomp_b = pl->tc.ncomp;
     a.nchunks = pl->tc.nchunks;
@@ -478,18 +578,19 @@ cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     }
     a.pn = pl->tc.pn;
     a.tmem_cols = (uint32_t)pl->tc.tmem_cols;
-    a.nslab_buf = pl->tc.nbuf;
+    a.nslab = pl->tc.nbuf;
     a.nbslots = pl->tc.nbslots;
-    const int half = lv.n >> 1;
     a.tiles_x = (half + 7) / 8;
     a.tiles_y = (half + 15) / 16;
     const unsigned blocks = (unsigned)(8 * a.tiles_x * a.tiles_y * half);
+    const CUtensorMap &mh = *reinterpret_cast<const CUtensorMap *>(&pl->tc.maps[level][0]);
+    const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(&pl->tc.maps[level][1]);
     pl->launches[FC2T2_STAGE_M2L] += 1;
     const int key = pl->tc.mode * 8 + (a.pn <= 32 ? 0 : a.pn <= 64 ? 1 : a.pn <= 96 ? 2 : a.pn <= 128 ? 3 : 4);
 #define FC2T2_TC_CASE(MODE_, IDX_, PN_)                                                                   \
     case (MODE_) * 8 + (IDX_):                                                                           \
         cudaFuncSetAttribute(k_m2l_tc<MODE_, PN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->tc.smem); \
-        k_m2l_tc<MODE_, PN_><<<blocks, kTcThreads, pl->tc.smem, s>>>(a);                                  \
+        k_m2l_tc<MODE_, PN_><<<blocks, kTcThreads, pl->tc.smem, s>>>(mh, ml, a);                          \
         break;
     switch (key) {
         FC2T2_TC_CASE(0, 0, 32) FC2T2_TC_CASE(0, 1, 64) FC2T2_TC_CASE(0, 2, 96) FC2T2_TC_CASE(0, 3, 128) FC2T2_TC_CASE(0, 4, 176)

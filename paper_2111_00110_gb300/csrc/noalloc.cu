@@ -259,6 +259,8 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
         }
     }
     for (int t = 0; t < 3; ++t) h_start[t][P] = cnt[t];
+    pl.n_m2m_pairs = cnt[0];
+    pl.n_l2l_pairs = cnt[1];
 
     // pageable host-to-device copies return once the host data has been staged
     struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
