@@ -1,17 +1,22 @@
 #!/usr/bin/env python
 """Benchmark of the FC2T2 transform: forward + backward query-evaluations per second.
 
-Workload (default, ``uniform3d``): 3D, N = M = 2^20 sources and queries uniform in [0,1)^3,
-w ~ N(0,1), Gaussian sigma = 0.02, 64^3 finest grid (5 levels), order 6 (84 coefficients per
-cell); one step = forward y = f(q; p, w) plus backward (wbar, pbar) for the cotangent
-ybar = y (L = sum y^2 / 2), all through the C ABI.  Metric: M / (t_fwd + t_bwd).
+Workload (``uniform3d``): 3D, N = M = 2^20 sources and queries uniform in [0,1)^3, w ~ N(0,1),
+Gaussian sigma = 0.02, 64^3 finest grid (5 levels), order 6 (84 coefficients per cell).  One step =
+forward y = f(q; p, w) plus backward (wbar, pbar) for the cotangent ybar = y (L = sum y^2 / 2), all
+through the C ABI.  Metric: M / (t_fwd + t_bwd) at a stated relative-L2 error against the FP64
+oracle.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--m2l fp32]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--m2l MODE]
 
-Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle on the host
-cores on a bounded sample of the same workload (the queries -- and, for the backward, the
-sources -- with z < 1/8, about an eighth of each; the oracle evaluates only the cells these
-need), reported in the same unit.
+MODE "auto" (default) reports the FP32-accurate path (M2L on tcgen05 with TF32 x 3 operands) as
+`value`, and the mixed-precision form (single TF32 M2L) and the plain CUDA-core FP32 form as
+`variants`, each with its measured error against the oracle on a seeded sample (4096 queries for
+y, 4096 sources for wbar and pbar with a fixed seeded cotangent).
+
+Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle on the host cores
+on a bounded sample of the same workload (the queries -- and, for the backward, the sources --
+with z < 1/8, about an eighth of each; the oracle evaluates only the cells these need).
 """
 from __future__ import annotations
 
@@ -31,6 +36,8 @@ if ROOT not in sys.path:
 
 METRIC = "fwd+bwd query-evals/s"
 UNIT = "query-evals/s"
+# nominal dense tensor-core ratios (TF32 : BF16 = 1.1 : 2.25 PFLOP/s per GPU)
+TF32_PER_BF16 = 1.1 / 2.25
 
 
 def parse():
@@ -39,9 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--m2l", default="fp32")
+    ap.add_argument("--m2l", default="auto", choices=["auto", "tf32x3", "tf32", "bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
     return ap.parse_args()
 
 
@@ -50,33 +58,20 @@ def dist_env():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
-# --------------------------------------------------------------------------- arithmetic
-
-def m2l_pairs_per_level(D: int, n: int):
-    """Exact number of (target, source) cell pairs M2L visits per level: the parity window
-    clipped to the grid, minus the 3^D hole above the finest level (per-dimension sums
-    factorise because window and hole are products over dimensions)."""
-    out, nl, lev = [], n, 0
-    while nl >= 4:
-        W = H = 0
-        for t in range(nl):
-            lo = -3 if t & 1 else -2
-            W += sum(1 for o in range(lo, lo + 6) if 0 <= t + o < nl)
-            H += sum(1 for o in (-1, 0, 1) if 0 <= t + o < nl)
-        out.append(W ** D - (H ** D if lev > 0 else 0))
-        nl //= 2
-        lev += 1
-    return out
-
-
-def m2l_useful_flops(D: int, n: int, rho: int) -> int:
-    """2 * C(rho + 2D, 2D) multiply-adds per interacting cell pair (|k| + |b| <= rho)."""
-    return 2 * math.comb(rho + 2 * D, 2 * D) * sum(m2l_pairs_per_level(D, n))
-
-
 def fp32_peak_tflops(sm_mhz: float) -> float:
     """152 SMs x 128 FP32 lanes x 2 FLOP per FMA x clock."""
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def aggregate_max(value: float, world: int, device=None) -> float:
+    """Max over ranks (timing); identity on one rank."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------------------- clocks
@@ -162,6 +157,27 @@ def cpu_oracle_step(wl, sel_q, sel_p):
     return time.perf_counter() - t0
 
 
+def oracle_reference_sample(wl, n=4096, seed=12345):
+    """Oracle y at n seeded queries, and (wbar, pbar) at n seeded sources for the seeded
+    cotangent wl.ybar() -- the accuracy reference for every M2L form."""
+    import numpy as np
+    import oracle
+    oracle.build()
+    rng = np.random.default_rng(seed)
+    sq = np.sort(rng.choice(wl.M, size=n, replace=False))
+    sp = np.sort(rng.choice(wl.N, size=n, replace=False))
+    d = oracle.OracleDesc(dim=3, grid=wl.grid, order=wl.order, sigma=wl.sigma)
+    p, w, q = (np.asarray(a, dtype=np.float64) for a in (wl.p, wl.w, wl.q))
+    y = oracle.forward(d, p, w, q, sel=sq)
+    wb, pb = oracle.backward(d, p, w, q, np.asarray(wl.ybar(), dtype=np.float64), sel=sp)
+    return {"sq": sq, "sp": sp, "y": y, "wbar": wb, "pbar": pb}
+
+
+def rel_l2(a, b):
+    import numpy as np
+    return float(np.linalg.norm(np.asarray(a, np.float64) - b) / np.linalg.norm(b))
+
+
 def run_reference(args, rank, world):
     """The oracle on the host cores, bounded sample per step (rank 0 only)."""
     if rank != 0:
@@ -194,41 +210,52 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, rank, world, local_rank):
-    import numpy as np
-    import torch
-    import torch.distributed as dist
+# ---------------------------------------------------------------------------- our path
 
-    from paper_2111_00110_gb300 import build as _build
-    from paper_2111_00110_gb300 import workloads
+class Measured:
+    pass
+
+
+def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, clocks=False):
+    """Time `args.steps` fwd+bwd steps of one M2L form; per-stage device times from the library's
+    events on the launching stream; optional end-to-end loop from pinned host buffers."""
+    import torch
     from paper_2111_00110_gb300.transform import Plan
 
-    _build.build()
-    torch.cuda.set_device(local_rank)
-    dev = torch.device("cuda", local_rank)
-    # weak scaling: every rank transforms its own independent point set
-    wl = workloads.uniform3d(seed=2 + rank)
-    D, n, rho = 3, wl.grid, wl.order
-    plan = Plan(D, n, rho, wl.sigma, m2l=args.m2l, max_sources=wl.N, max_queries=wl.M, device=dev)
+    plan = Plan(3, wl.grid, wl.order, wl.sigma, m2l=mode, max_sources=wl.N, max_queries=wl.M, device=dev)
     p = torch.from_numpy(wl.p).to(dev)
     w = torch.from_numpy(wl.w).to(dev)
     q = torch.from_numpy(wl.q).to(dev)
     stream = torch.cuda.current_stream(dev)
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def step():
         y = plan.forward(p, w, q)
         plan.backward(p, w, q, y)
 
-    for _ in range(max(args.warmup, 3 if args.warmup >= 3 else args.warmup)):
+    out = Measured()
+    out.mode = mode
+    out.info = plan.info()
+    # accuracy against the oracle sample (a seeded cotangent for the backward)
+    if ref is not None:
+        y = plan.forward(p, w, q)
+        wb, pb = plan.backward(p, w, q, torch.from_numpy(wl.ybar()).to(dev))
+        torch.cuda.synchronize(dev)
+        out.err = {"y": rel_l2(y.cpu().numpy()[ref["sq"]], ref["y"]),
+                   "wbar": rel_l2(wb.cpu().numpy()[ref["sp"]], ref["wbar"]),
+                   "pbar": rel_l2(pb.cpu().numpy()[ref["sp"]], ref["pbar"])}
+    else:
+        out.err = None
+    for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     plan.profile(True)
     plan.profile_read(reset=True)
-    clocks = ClockSampler(local_rank)
-    clocks.start()
+    sampler = ClockSampler(dev.index) if clocks else None
+    if sampler:
+        sampler.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     torch.cuda.synchronize(dev)
@@ -238,25 +265,21 @@ def run_ours(args, rank, world, local_rank):
         step()
         ends[i].record(stream)
     torch.cuda.synchronize(dev)
-    clk = clocks.stop()
+    out.clocks = sampler.stop() if sampler else None
     stage_ms, launches = plan.profile_read(reset=True)
     plan.profile(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
-    value = wl.M * args.steps * world / (total_ms / 1e3)
-
-    # ---- end to end through the C ABI with host buffers (pinned), copies inside the timing
-    e2e = None
-    if not args.no_e2e:
+    total_ms = aggregate_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
+    out.ms_per_step = total_ms / args.steps
+    out.value = wl.M * args.steps * world / (total_ms / 1e3)
+    out.stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    out.launches = int(sum(launches.values()))
+    out.launches_per_step = {k: v / args.steps for k, v in launches.items()}
+    out.e2e = None
+    if do_e2e:
         hp, hw, hq = (torch.from_numpy(a).pin_memory() for a in (wl.p, wl.w, wl.q))
         dp, dw, dq = torch.empty_like(p), torch.empty_like(w), torch.empty_like(q)
         hwb = torch.empty(wl.N, dtype=torch.float32).pin_memory()
-        hpb = torch.empty(wl.N, D, dtype=torch.float32).pin_memory()
+        hpb = torch.empty(wl.N, 3, dtype=torch.float32).pin_memory()
 
         def e2e_step():
             dp.copy_(hp, non_blocking=True)
@@ -276,32 +299,64 @@ def run_ours(args, rank, world, local_rank):
             e2e_step()
         ee.record(stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = es.elapsed_time(ee)
-        if world > 1:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        h2d = 4 * (wl.N * D + wl.N + wl.M * D)
-        d2h = 4 * (wl.N + wl.N * D)
-        e2e = {"value": wl.M * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e2e_ms = aggregate_max(es.elapsed_time(ee), world, dev)
+        out.e2e = {"value": wl.M * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+                   "h2d_bytes_per_step": 4 * (wl.N * 3 + wl.N + wl.M * 3),
+                   "d2h_bytes_per_step": 4 * (wl.N + wl.N * 3)}
+    plan.close()
+    return out
 
+
+def roofline_for(m: Measured, peaks):
+    """Roofline of the dominant kernel (M2L) for one measured form."""
+    m2l_ms = m.stage_ms["m2l"]                       # per step = two transforms
+    useful = 2 * m.info["m2l_useful_flops"]
+    issued = 2 * m.info["m2l_issued_flops"]
+    if m.mode == "fp32":
+        sm = peaks.get("sm_max_mhz", 2070.0)
+        peak = fp32_peak_tflops(sm)
+        achieved = useful / (m2l_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "m2l (CUDA cores, FP32)", "flops_per_step": useful,
+                "peak_basis": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm:.0f} MHz"}
+    bf16 = peaks.get("bf16_tflops_sustained")
+    basis = "measured bf16 sustained (MEASURED_PEAKS.json)"
+    if bf16 is None:
+        bf16, basis = 1700.0, "fallback bf16 sustained"
+    peak = bf16 if m.mode == "bf16" else bf16 * TF32_PER_BF16
+    if m.mode != "bf16":
+        basis += " x nominal TF32/BF16 ratio 1.1/2.25"
+    achieved = issued / (m2l_ms / 1e3) / 1e12
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": f"m2l (tcgen05, {m.mode}) incl. its pack pass",
+            "flops_per_step": issued, "useful_flops_per_step": useful,
+            "useful_achieved": useful / (m2l_ms / 1e3) / 1e12, "peak_basis": basis}
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2111_00110_gb300 import build as _build
+    from paper_2111_00110_gb300 import workloads
+
+    _build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    # weak scaling: every rank transforms its own independent point set
+    wl = workloads.uniform3d(seed=2 + rank)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    ref = None
+    if not args.no_check and rank == 0:
+        ref = oracle_reference_sample(wl)
+    primary = "tf32x3" if args.m2l == "auto" else args.m2l
+    main = measure_mode(primary, wl, args, world, dev, flush, ref=ref, do_e2e=not args.no_e2e, clocks=True)
+    variants = {}
+    if args.m2l == "auto":
+        for mode in ("tf32", "fp32"):
+            variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref)
     if rank != 0:
         return
-    # ---- roofline of the dominant kernel (M2L; CUDA cores in FP32)
     peaks = load_peaks()
-    m2l_flops = 2 * m2l_useful_flops(D, n, rho)            # forward + backward transforms
-    m2l_ms = stage_ms["m2l"] / args.steps
-    m2l_launches = launches["m2l"] / args.steps
-    achieved = m2l_flops / (m2l_ms / 1e3) / 1e12
-    sm_max = peaks.get("sm_max_mhz", 2070.0)
-    peak = fp32_peak_tflops(sm_max)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "m2l", "flops_per_step": m2l_flops, "launches_per_step": m2l_launches,
-                "peak_basis": f"FP32 FMA: 152 SMs x 128 lanes x 2 x {sm_max:.0f} MHz"}
-    step_stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
-
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -317,26 +372,28 @@ def run_ours(args, rank, world, local_rank):
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {exc}"}
 
+    def summary(m: Measured):
+        return {"value": m.value, "ms_per_step": m.ms_per_step, "rel_l2_vs_oracle": m.err,
+                "stage_ms_per_step": m.stage_ms, "roofline": roofline_for(m, peaks)}
+
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": main.value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": main.ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "uniform3d", "dim": D, "N": wl.N, "M": wl.M, "grid": n,
-                   "levels": plan_levels(n), "order": rho, "sigma": wl.sigma, "m2l": args.m2l,
+        "config": {"workload": "uniform3d", "dim": 3, "N": wl.N, "M": wl.M, "grid": wl.grid,
+                   "levels": main.info["levels"], "order": wl.order, "sigma": wl.sigma, "m2l": primary,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"{world} independent replicas" if world > 1 else "single GPU"},
-        "clocks": clk,
-        "e2e": e2e,
-        "gpu_launches": int(sum(launches.values())),
-        "roofline": roofline,
-        "stage_ms_per_step": step_stage_ms,
+        "rel_l2_vs_oracle": main.err,
+        "clocks": main.clocks,
+        "e2e": main.e2e,
+        "gpu_launches": main.launches,
+        "roofline": roofline_for(main, peaks),
+        "stage_ms_per_step": main.stage_ms,
+        "variants": {k: summary(v) for k, v in variants.items()},
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)
-
-
-def plan_levels(n: int) -> int:
-    return int(math.log2(n)) - 1
 
 
 def main():

@@ -130,6 +130,36 @@ FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
                             const float *q, int64_t M, const float *ybar,
                             float *wbar, float *pbar);
 
+/* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
+ * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,
+ * each of n_inst entries) with N[i] sources and M[i] queries.  All instances are enqueued on
+ * `stream` in order; the call is equivalent to n_inst calls of fc2t2_forward / fc2t2_backward and
+ * can be captured into a CUDA graph by the caller (with check_domain off).  Two instances may
+ * share a plan (they run one after the other).  Errors: INVALID_ARG (n_inst < 0, a NULL array),
+ * and any error of the single-instance call, for the first failing instance. */
+FC2T2_API fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream,
+                                             const float *const *p, const float *const *w, const int64_t *N,
+                                             const float *const *q, const int64_t *M, float *const *y);
+FC2T2_API fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *stream,
+                                              const float *const *p, const float *const *w, const int64_t *N,
+                                              const float *const *q, const int64_t *M,
+                                              const float *const *ybar, float *const *wbar, float *const *pbar);
+
+/* What a plan computes per transform (forward or backward), for performance accounting. */
+typedef struct {
+    int levels;                  /* grid levels (finest n, coarsest 4 cells per dimension) */
+    int coefficients;            /* P = C(order + dim, dim) per cell */
+    int m2l_tensor_cores;        /* 1: the finest level's M2L runs on tcgen05 */
+    double m2l_cell_pairs;       /* interacting (target, source) cell pairs over all levels */
+    double m2l_useful_flops;     /* 2 x #{(k, b): |k| + |b| <= order} x m2l_cell_pairs */
+    double m2l_issued_flops;     /* multiply-add work (x2) the M2L kernels issue, incl. the zeros
+                                    inside the dense tensor-core blocks; = useful on CUDA cores */
+    int64_t device_bytes;        /* device memory owned by the plan */
+} fc2t2_plan_info;
+
+/* Fill *info for `plan`.  Errors: INVALID_ARG (NULL argument). */
+FC2T2_API fc2t2_status fc2t2_plan_query(fc2t2_plan plan, fc2t2_plan_info *info);
+
 /* Pipeline stages, for fc2t2_profile_read. */
 typedef enum {
     FC2T2_STAGE_SORT = 0,        /* binning + counting sort of sources and queries */

@@ -37,6 +37,9 @@ EXPORTS = (
     "fc2t2_profile_enable",
     "fc2t2_profile_read",
     "fc2t2_forward_noalloc",
+    "fc2t2_forward_batched",
+    "fc2t2_backward_batched",
+    "fc2t2_plan_query",
 )
 STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p")
 
@@ -57,6 +60,18 @@ class PlanDesc(ctypes.Structure):
         ("check_domain", ctypes.c_int),
         ("max_sources", ctypes.c_int64),
         ("max_queries", ctypes.c_int64),
+    ]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("coefficients", ctypes.c_int),
+        ("m2l_tensor_cores", ctypes.c_int),
+        ("m2l_cell_pairs", ctypes.c_double),
+        ("m2l_useful_flops", ctypes.c_double),
+        ("m2l_issued_flops", ctypes.c_double),
+        ("device_bytes", ctypes.c_int64),
     ]
 
 
@@ -91,9 +106,13 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_profile_enable.argtypes = [vp, ctypes.c_int]
         lib.fc2t2_profile_read.argtypes = [vp, vp, vp, ctypes.c_int]
         lib.fc2t2_forward_noalloc.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
+        lib.fc2t2_forward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.fc2t2_backward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.fc2t2_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
-                     "fc2t2_forward_noalloc"):
+                     "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
+                     "fc2t2_plan_query"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -136,3 +155,44 @@ def profile_read(plan: int, reset: bool = False):
     n = (ctypes.c_int64 * len(STAGES))()
     check(load().fc2t2_profile_read(plan, ctypes.addressof(ms), ctypes.addressof(n), 1 if reset else 0))
     return dict(zip(STAGES, list(ms))), dict(zip(STAGES, list(n)))
+
+
+def plan_query(plan: int) -> dict:
+    info = PlanInfo()
+    check(load().fc2t2_plan_query(plan, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in PlanInfo._fields_}
+
+
+def _ptr_array(ptrs):
+    arr = (ctypes.c_void_p * len(ptrs))(*[p or None for p in ptrs])
+    return arr
+
+
+def forward_batched(plans, stream, p, w, N, q, M, y) -> None:
+    """Batched forward: lists of plan handles, device pointers and sizes, one entry per instance."""
+    n = len(plans)
+    i64 = ctypes.c_int64 * n
+    check(load().fc2t2_forward_batched(n, ctypes.addressof(_keep(_ptr_array(plans))), stream,
+                                       ctypes.addressof(_keep(_ptr_array(p))), ctypes.addressof(_keep(_ptr_array(w))),
+                                       ctypes.addressof(_keep(i64(*N))), ctypes.addressof(_keep(_ptr_array(q))),
+                                       ctypes.addressof(_keep(i64(*M))), ctypes.addressof(_keep(_ptr_array(y)))))
+    _kept.clear()
+
+
+def backward_batched(plans, stream, p, w, N, q, M, ybar, wbar, pbar) -> None:
+    n = len(plans)
+    i64 = ctypes.c_int64 * n
+    check(load().fc2t2_backward_batched(n, ctypes.addressof(_keep(_ptr_array(plans))), stream,
+                                        ctypes.addressof(_keep(_ptr_array(p))), ctypes.addressof(_keep(_ptr_array(w))),
+                                        ctypes.addressof(_keep(i64(*N))), ctypes.addressof(_keep(_ptr_array(q))),
+                                        ctypes.addressof(_keep(i64(*M))), ctypes.addressof(_keep(_ptr_array(ybar))),
+                                        ctypes.addressof(_keep(_ptr_array(wbar))), ctypes.addressof(_keep(_ptr_array(pbar)))))
+    _kept.clear()
+
+
+_kept = []
+
+
+def _keep(obj):
+    _kept.append(obj)
+    return obj

@@ -499,6 +499,65 @@ fc2t2_status fc2t2_profile_read(fc2t2_plan pl, double *ms, int64_t *launches, in
     return st;
 }
 
+fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
+                                   const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
+                                   float *const *y) {
+    if (n_inst < 0) return set_error(FC2T2_ERR_INVALID_ARG, "n_inst < 0");
+    if (n_inst == 0) return FC2T2_OK;
+    if (!plans || !p || !w || !N || !q || !M || !y) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    for (int i = 0; i < n_inst; ++i) {
+        const fc2t2_status st = fc2t2_forward(plans[i], stream, p[i], w[i], N[i], q[i], M[i], y[i]);
+        if (st != FC2T2_OK) return st;
+    }
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
+                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
+                                    const float *const *ybar, float *const *wbar, float *const *pbar) {
+    if (n_inst < 0) return set_error(FC2T2_ERR_INVALID_ARG, "n_inst < 0");
+    if (n_inst == 0) return FC2T2_OK;
+    if (!plans || !p || !w || !N || !q || !M || !ybar || !wbar || !pbar)
+        return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    for (int i = 0; i < n_inst; ++i) {
+        const fc2t2_status st = fc2t2_backward(plans[i], stream, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
+        if (st != FC2T2_OK) return st;
+    }
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {
+    if (!pl || !info) return set_error(FC2T2_ERR_INVALID_ARG, "NULL argument");
+    info->levels = pl->nlev;
+    info->coefficients = pl->P;
+    info->m2l_tensor_cores = (pl->tc.enabled && pl->tc.level_ok[0]) ? 1 : 0;
+    // interacting cell pairs per level: per-dimension window sums factorise
+    double pairs_total = 0.0, issued = 0.0;
+    double q = 1.0;   // #{(k, b) : |k| + |b| <= rho} = C(rho + 2D, 2D)
+    for (int i = 1; i <= 2 * pl->D; ++i) q = q * (pl->rho + i) / i;
+    for (int l = 0; l < pl->nlev; ++l) {
+        const int nl = pl->lev[l].n;
+        double W = 0.0, H = 0.0;
+        for (int t = 0; t < nl; ++t) {
+            const int lo = (t & 1) ? -3 : -2;
+            for (int o = lo; o < lo + 6; ++o) W += (t + o >= 0 && t + o < nl) ? 1.0 : 0.0;
+            for (int o = -1; o <= 1; ++o) H += (t + o >= 0 && t + o < nl) ? 1.0 : 0.0;
+        }
+        const double pairs = std::pow(W, pl->D) - (l > 0 ? std::pow(H, pl->D) : 0.0);
+        pairs_total += pairs;
+        if (pl->tc.enabled && pl->tc.level_ok[l]) issued += pl->tc.mma_flops_level[l];
+        else issued += 2.0 * q * pairs;
+    }
+    info->m2l_cell_pairs = pairs_total;
+    info->m2l_useful_flops = 2.0 * q * pairs_total;
+    info->m2l_issued_flops = issued;
+    int64_t bytes = 2 * pl->G_total * pl->Pp * (int64_t)sizeof(float);
+    bytes += (int64_t)pl->mma_ops_bytes + pl->tc.packed_bytes;
+    bytes += (pl->src.cap + pl->qry.cap) * (int64_t)(5 * sizeof(int) + (pl->D + 1) * sizeof(float));
+    info->device_bytes = bytes;
+    return FC2T2_OK;
+}
+
 const char *fc2t2_status_string(fc2t2_status st) {
     switch (st) {
         case FC2T2_OK: return "ok";

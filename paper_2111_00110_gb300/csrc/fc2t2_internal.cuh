@@ -112,9 +112,11 @@ struct fc2t2_plan_s {
     size_t mma_ops_bytes = 0;
     struct TcInfo {
         int enabled = 0, mode = 0, img_bytes = 0, ncomp = 1, pn = 0, kbytes = 0, nchunks = 0;
-        int n0[4] = {0, 0, 0, 0}, N[4] = {0, 0, 0, 0}, K[4] = {0, 0, 0, 0}, b_off[4] = {0, 0, 0, 0};
+        int n0[24] = {}, N[24] = {}, K[24] = {}, b_off[24] = {};
         int nbuf = 1, nbslots = 2, smem = 0, tmem_cols = 32;
         double mma_flops = 0.0;                       // tensor-core work issued per transform
+        double mma_flops_level[fc2t2::kMaxLevels] = {};
+        int64_t packed_bytes = 0;
         void *packed[fc2t2::kMaxLevels] = {};         // moments in the tensor-core layout, per level
         int level_ok[fc2t2::kMaxLevels] = {};         // 1: this level runs on the tensor cores
         alignas(64) unsigned char maps[fc2t2::kMaxLevels][2][128] = {};   // TMA descriptors (hi, lo)
@@ -148,6 +150,9 @@ cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w);
 cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+// register-resident M2M / L2L for orders <= 6 (return false when not applicable)
+bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);
+bool launch_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);
 fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
 
 }  // namespace fc2t2

@@ -14,10 +14,12 @@
 // load brings the 10 x 18 cell "slab" of sub-grid sigma around the tile into shared memory
 // (cells outside the grid arrive as zeros).  The nine (delta_x, delta_y) A operands of a slab
 // are views that differ only in their start address.  The operators B_o are precomputed per
-// level as shared-memory images and fetched with bulk copies.  Because |k| + |b| <= rho, the
-// k range is cut into chunks that only run over the b range they can reach (degree-block
-// skipping), e.g. rho = 6: k in [0,16) x b < 96, [16,32) x b < 32, [32,96) x b < 16 -- 3072 of
-// 9216 dense multiply-adds.
+// level as shared-memory images and fetched with bulk copies.  Because |k| + |b| <= rho, each
+// MMA K-step (16 BF16 or 8 TF32 values of b) only reaches the k of degree <= rho - min|b| of
+// the step, so its N shrinks with the degree of b (degree-block skipping): rho = 6, BF16 uses
+// N = 96, 32, 16, 16, 16, 16 for its six K-steps -- 3072 of 9216 dense multiply-adds.  (An
+// MMA instruction costs at least ~40 cycles whatever its size and runs at full rate only from
+// N ~ 96, so one instruction per K-step is cheaper than splitting k into narrow chunks.)
 //
 // Precision: BF16 or TF32 operands with FP32 accumulation, or TF32 x 3 (A_hi B_hi + A_hi B_lo
 // + A_lo B_hi, the low parts being the TF32 rounding residues), accurate to FP32.  The tensor
@@ -42,13 +44,14 @@ using namespace tc;
 
 constexpr int kTcThreads = 192;
 constexpr int kSlabCells = 180;          // 10 x 18 cells
-constexpr int kMaxChunks = 4;
+constexpr int kMaxChunks = 24;           // K-steps per operator (b up to 176 TF32 values)
 constexpr int kMaxBSlots = 8;
 constexpr int kMaxSlabSlots = 3;
 
 struct TcChunk {
-    int n0, N, K;     // k columns [n0, n0 + N), b range [0, K)
+    int n0, N, K;     // k columns [n0, n0 + N) over the b range [k0, k0 + K) of one K-step
     int b_off;        // byte offset of the chunk's block inside one operator image
+    int k0;
 };
 
 struct TcArgs {
@@ -79,12 +82,12 @@ struct TcMode {
     static constexpr uint32_t fmt = MODE == 0 ? 1u : 2u;
 };
 
-__device__ __forceinline__ void tma_load_5d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            int c4, uint64_t *bar) {
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-        "%6}], [%7];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+        "[%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
         : "memory");
 }
 
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ uint64_t bar_bfull[kMaxBSlots], bar_bfree[kMaxBSlots], bar_sfull[kMaxSlabSlots], bar_sfree[kMaxSlabSlots];
     __shared__ uint64_t bar_accfull[2], bar_accfree[2], bar_done;
     __shared__ uint32_t tmem_base;
+    __shared__ int2 s_chunk[kMaxChunks];         // (N, b_off) of each K-step
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int half = args.nl >> 1;
@@ -164,6 +168,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     unsigned char *bring = smem + ((args.nslab * slab_stride + 1023) & ~1023);
     const int bslot_bytes = args.img_bytes * args.ncomp_b;
 
+    if (threadIdx.x < kMaxChunks) s_chunk[threadIdx.x] = make_int2(args.ch[threadIdx.x].N, args.ch[threadIdx.x].b_off);
     if (threadIdx.x == 0) {
         for (int i = 0; i < args.nbslots; ++i) { mbar_init(&bar_bfull[i], 1); mbar_init(&bar_bfree[i], 1); }
         for (int i = 0; i < args.nslab; ++i) { mbar_init(&bar_sfull[i], 1); mbar_init(&bar_sfree[i], 1); }
@@ -178,11 +183,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const uint32_t tacc = tmem_base;
 
     bool ok = true;
-    int c_n0[kMaxChunks], c_N[kMaxChunks], c_K[kMaxChunks], c_boff[kMaxChunks];
-#pragma unroll
-    for (int c = 0; c < kMaxChunks; ++c) {
-        c_n0[c] = args.ch[c].n0; c_N[c] = args.ch[c].N; c_K[c] = args.ch[c].K; c_boff[c] = args.ch[c].b_off;
-    }
     // operators of step s = (sigma, dz), then (dx, dy); the hole is skipped above the finest level
     auto op_of = [&](int s, int dx, int dy, int &olin) -> bool {
         const int sg = s / 3, dz = s % 3 - 1;
@@ -203,8 +203,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 unsigned char *dst = slabs + slot * slab_stride;
                 // z plane index includes the zero plane below z = 0
                 const int zc = sg * (half + 2) + (az + dz + 1);
-                tma_load_5d(dst, &map_hi, 0, ax0 - 1, ay0 - 1, 0, zc, &bar_sfull[slot]);
-                if (MODE == 2) tma_load_5d(dst + slab_bytes, &map_lo, 0, ax0 - 1, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                // innermost coordinate in bytes: (ax0 - 1) * 16, a multiple of 16 (may be -16: zero fill)
+                tma_load_4d(dst, &map_hi, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                if (MODE == 2) tma_load_4d(dst + slab_bytes, &map_lo, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
                 for (int t9 = 0; t9 < 9 && ok; ++t9) {
                     int olin;
                     if (!op_of(s, t9 % 3 - 1, t9 / 3 - 1, olin)) continue;
@@ -227,7 +228,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         if (lane == 0) {
             // ---------------------------------------------------------------- MMA issuer
             const uint32_t lboA = kSlabCells * 16, sboA = 160;
-            const uint64_t a_step = (uint64_t)((2u * lboA) >> 4);      // descriptor increment per K-step
             int j = 0;
             for (int s = 0; s < 24 && ok; ++s) {
                 const int slot = s % args.nslab, use = s / args.nslab;
@@ -247,30 +247,23 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     tc_fence_after();
                     const uint32_t b_img = smem_u32(bring + bslot * bslot_bytes);
                     const uint32_t a_view = slab_a + (uint32_t)(((dy + 1) * 10 + (dx + 1)) * 16);
-#pragma unroll
-                    for (int c = 0; c < kMaxChunks; ++c) {
-                        if (c >= args.nchunks) break;
-                        const uint32_t lboB = (uint32_t)(c_N[c] / 8) * 128u;
-                        const uint64_t b_step = (uint64_t)((2u * lboB) >> 4);
-                        const uint32_t idesc = instr_desc(Md::fmt, (uint32_t)c_N[c]);
-                        const uint32_t dcol = acc_col + (uint32_t)c_n0[c];
-                        const int nks = c_K[c] / Md::eps;
+                    // one MMA per K-step; K-step 0 spans all Pn columns and initialises them
+                    for (int c = 0; c < args.nchunks; ++c) {
+                        const int2 cn = s_chunk[c];
+                        const uint32_t lboB = (uint32_t)(cn.x / 8) * 128u;
+                        const uint32_t idesc = instr_desc(Md::fmt, (uint32_t)cn.x);
+                        const uint32_t aoff = (uint32_t)c * 2u * lboA;
 #pragma unroll
                         for (int pass = 0; pass < (MODE == 2 ? 3 : 1); ++pass) {
-                            uint64_t ad = smem_desc(a_view + (pass == 2 ? (uint32_t)slab_bytes : 0u), lboA, sboA);
-                            uint64_t bd = smem_desc(b_img + (uint32_t)c_boff[c] + (pass == 1 ? (uint32_t)args.img_bytes : 0u),
-                                                    lboB, 128u);
-                            uint32_t accum = (started >> c) & 1u;
-                            for (int ks = 0; ks < nks; ++ks) {
-                                if (MODE == 0) mma_bf16(dcol, ad, bd, idesc, accum);
-                                else mma_tf32(dcol, ad, bd, idesc, accum);
-                                ad += a_step;
-                                bd += b_step;
-                                accum = 1u;
-                            }
-                            started |= 1u << c;
+                            const uint64_t ad = smem_desc(a_view + aoff + (pass == 2 ? (uint32_t)slab_bytes : 0u), lboA, sboA);
+                            const uint64_t bd = smem_desc(b_img + (uint32_t)cn.y + (pass == 1 ? (uint32_t)args.img_bytes : 0u),
+                                                          lboB, 128u);
+                            const uint32_t accum = (started || c > 0 || pass > 0) ? 1u : 0u;
+                            if (MODE == 0) mma_bf16(acc_col, ad, bd, idesc, accum);
+                            else mma_tf32(acc_col, ad, bd, idesc, accum);
                         }
                     }
+                    started = 1;
                     mma_commit(&bar_bfree[bslot]);
                     ++j;
                 }
@@ -335,40 +328,23 @@ int degree_of(int D, int k) {
     return d;
 }
 
-// Split [0, Pn) into at most kMaxChunks column chunks (multiples of 16) minimising the dense
-// multiply-adds sum N_c K_c, where chunk c only needs b of degree <= rho - deg(first k).
+// One chunk per MMA K-step of kg values of b: the step starting at b0 only reaches the k of
+// degree <= rho - deg(b0), i.e. the first ncoef(rho - deg(b0)) columns (rounded up to 16).
 void plan_chunks(int D, int rho, int P, int kg, std::vector<TcChunk> &out, int &pn, int &kfull) {
     pn = (P + 15) / 16 * 16;
-    const int nb = pn / 16;
-    auto kneed = [&](int n0) {
-        const int d = degree_of(D, n0 < P ? n0 : P - 1);
-        const int cnt = ncoef(D, rho - d);
-        return (cnt + kg - 1) / kg * kg;
-    };
-    const long INF = 1L << 60;
-    std::vector<std::vector<long>> dp(nb + 1, std::vector<long>(kMaxChunks + 1, INF));
-    std::vector<std::vector<int>> nxt(nb + 1, std::vector<int>(kMaxChunks + 1, -1));
-    for (int c = 0; c <= kMaxChunks; ++c) dp[nb][c] = 0;
-    for (int i = nb - 1; i >= 0; --i)
-        for (int c = 1; c <= kMaxChunks; ++c)
-            for (int e = i + 1; e <= nb; ++e) {
-                const long cost = (long)(e - i) * 16 * kneed(16 * i) + dp[e][c - 1];
-                if (cost < dp[i][c]) { dp[i][c] = cost; nxt[i][c] = e; }
-            }
+    kfull = (P + kg - 1) / kg * kg;
     out.clear();
-    int i = 0, c = kMaxChunks;
-    kfull = 0;
-    while (i < nb) {
-        const int e = nxt[i][c];
+    for (int k0 = 0; k0 < kfull; k0 += kg) {
+        const int d = degree_of(D, k0);
+        const int need = ncoef(D, rho - d);
         TcChunk ch;
-        ch.n0 = 16 * i;
-        ch.N = 16 * (e - i);
-        ch.K = kneed(16 * i);
+        ch.k0 = k0;
+        ch.K = kg;
+        ch.n0 = 0;
+        ch.N = (need + 15) / 16 * 16;
+        if (ch.N > pn) ch.N = pn;
         ch.b_off = 0;
-        if (ch.K > kfull) kfull = ch.K;
         out.push_back(ch);
-        i = e;
-        --c;
     }
 }
 
@@ -415,7 +391,7 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     std::vector<TcChunk> ch;
     int pn = 0, kfull = 0;
     plan_chunks(pl->D, pl->rho, pl->P, kg, ch, pn, kfull);
-    if (pn > 176) return FC2T2_OK;
+    if (pn > 176 || (int)ch.size() > kMaxChunks) return FC2T2_OK;
     int off = 0;
     for (auto &c : ch) { c.b_off = off; off += c.N * c.K * esz; }
     const int img = off;
@@ -425,15 +401,15 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     // shared memory: slab ring + operator ring (two CTAs per SM when both fit in half of it)
     const int slab = ((kSlabCells * 16 * nkc + 1023) & ~1023) * ncomp;   // as in the kernel
     const int bslot = img * ncomp;
+    // prefer two CTAs per SM, then a deep operator ring (bulk-copy latency), then more slab slots
     int nslab = 0, nbs = 0, smem = 0;
     for (int budget : {112 * 1024, 220 * 1024}) {
-        for (int ns = kMaxSlabSlots; ns >= 1 && !nslab; --ns) {
-            if (ns < 2 && budget <= 112 * 1024) continue;
-            for (int nb = kMaxBSlots; nb >= 3; --nb) {
+        for (int nb = kMaxBSlots; nb >= 4 && !nslab; --nb)
+            for (int ns = kMaxSlabSlots; ns >= 1; --ns) {
+                if (ns < 2 && budget <= 112 * 1024) continue;
                 const int bytes = ((ns * slab + 1023) & ~1023) + nb * bslot;
                 if (bytes <= budget) { nslab = ns; nbs = nb; smem = bytes; break; }
             }
-        }
         if (nslab) break;
     }
     if (!nslab) return FC2T2_OK;   // too large for shared memory: the CUDA-core M2L runs instead
@@ -457,7 +433,7 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
             for (const TcChunk &c : ch)
                 for (int n = 0; n < c.N; ++n)
                     for (int k = 0; k < c.K; ++k) {
-                        const int kap = c.n0 + n, b = k;
+                        const int kap = c.n0 + n, b = c.k0 + k;
                         double v = 0.0;
                         if (kap < pl->P && b < pl->P && deg[kap] + deg[b] <= pl->rho) {
                             const int m = gidx3(ex[3 * kap] + ex[3 * b], ex[3 * kap + 1] + ex[3 * b + 1],
@@ -499,15 +475,17 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
             return set_error(FC2T2_ERR_OOM, "cudaMalloc failed for packed moments");
         }
         pl->tc.packed[l] = buf;
+        pl->tc.packed_bytes += (int64_t)(comp_bytes * ncomp);
         pl->tc.level_ok[l] = 1;
         if ((e = cudaMemset(buf, 0, comp_bytes * ncomp)) != cudaSuccess) return check_cuda(e, "clear packed moments");
         for (int comp = 0; comp < ncomp; ++comp) {
-            cuuint64_t dims[5] = {16, (cuuint64_t)half, (cuuint64_t)half, (cuuint64_t)nkc, (cuuint64_t)8 * (half + 2)};
-            cuuint64_t strides[4] = {16, (cuuint64_t)16 * half, (cuuint64_t)16 * half * half,
+            // bytes of a row of x cells innermost (160-byte box rows), then y, chunk, (sigma, z)
+            cuuint64_t dims[4] = {(cuuint64_t)16 * half, (cuuint64_t)half, (cuuint64_t)nkc, (cuuint64_t)8 * (half + 2)};
+            cuuint64_t strides[3] = {(cuuint64_t)16 * half, (cuuint64_t)16 * half * half,
                                      (cuuint64_t)16 * half * half * nkc};
-            cuuint32_t box[5] = {16, 10, 18, (cuuint32_t)nkc, 1};
-            cuuint32_t estr[5] = {1, 1, 1, 1, 1};
-            CUresult r = enc(reinterpret_cast<CUtensorMap *>(&pl->tc.maps[l][comp]), CU_TENSOR_MAP_DATA_TYPE_UINT8, 5,
+            cuuint32_t box[4] = {160, 18, (cuuint32_t)nkc, 1};
+            cuuint32_t estr[4] = {1, 1, 1, 1};
+            CUresult r = enc(reinterpret_cast<CUtensorMap *>(&pl->tc.maps[l][comp]), CU_TENSOR_MAP_DATA_TYPE_UINT8, 4,
                              static_cast<unsigned char *>(buf) + comp * comp_bytes, dims, strides, box, estr,
                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -537,7 +515,8 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     for (int l = 0; l < pl->nlev; ++l) {
         const int half = pl->lev[l].n >> 1;
         const double tiles = 8.0 * ((half + 7) / 8) * ((half + 15) / 16) * half;
-        total += tiles * (l == 0 ? 216 : 189) * per_op;
+        pl->tc.mma_flops_level[l] = tiles * (l == 0 ? 216 : 189) * per_op;
+        total += pl->tc.mma_flops_level[l];
     }
     pl->tc.mma_flops = total;
     pl->tc.enabled = 1;
@@ -574,7 +553,7 @@ cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     a.ncomp_b = pl->tc.ncomp;
     a.nchunks = pl->tc.nchunks;
     for (int i = 0; i < kMaxChunks; ++i) {
-        a.ch[i].n0 = pl->tc.n0[i]; a.ch[i].N = pl->tc.N[i]; a.ch[i].K = pl->tc.K[i]; a.ch[i].b_off = pl->tc.b_off[i];
+        a.ch[i].n0 = 0; a.ch[i].N = pl->tc.N[i]; a.ch[i].K = 0; a.ch[i].b_off = pl->tc.b_off[i]; a.ch[i].k0 = 0;
     }
     a.pn = pl->tc.pn;
     a.tmem_cols = (uint32_t)pl->tc.tmem_cols;

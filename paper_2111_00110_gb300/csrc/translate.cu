@@ -160,6 +160,8 @@ static int x_parents(const fc2t2_plan_s *pl, int npairs, bool l2l, size_t &smem)
 }
 
 cudaError_t launch_m2m(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
+    cudaError_t rerr = cudaSuccess;
+    if (launch_m2m_reg(pl, s, level, rerr)) return rerr;
     const Level &c = pl->lev[level], &p = pl->lev[level + 1];
     XTables tb{pl->d_m2m_start, pl->d_m2m_pairs, pl->n_m2m_pairs, pl->d_shift, pl->d_pow2};
     size_t smem = 0;
@@ -210,6 +212,8 @@ __global__ void __launch_bounds__(kXThreads) k_l2l(const float *__restrict__ Lp,
 }
 
 cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
+    cudaError_t rerr = cudaSuccess;
+    if (launch_l2l_reg(pl, s, level, rerr)) return rerr;
     const Level &p = pl->lev[level + 1], &c = pl->lev[level];
     XTables tb{pl->d_l2l_start, pl->d_l2l_pairs, pl->n_l2l_pairs, pl->d_shift, pl->d_pow2};
     size_t smem = 0;

@@ -80,6 +80,10 @@ class Plan:
         """(ms per stage, kernel launches per stage) accumulated since the last reset."""
         return capi.profile_read(self._h, reset)
 
+    def info(self) -> dict:
+        """Per-transform work of this plan (levels, P, M2L cell pairs and flops, device bytes)."""
+        return capi.plan_query(self._h)
+
     def _stream(self) -> int:
         return torch.cuda.current_stream(self.device).cuda_stream
 
