@@ -139,6 +139,17 @@ __global__ void __launch_bounds__(256) k_pack_tc(const float *__restrict__ M, un
 }
 
 // ------------------------------------------------------------------------------ M2L
+// most K-steps any order up to the one that needs PNMAX columns can have (BF16: 16 b per step,
+// TF32: 8); the issue loop is unrolled to it and predicates off the steps a plan does not use
+template <int MODE, int PNMAX>
+constexpr int max_ksteps() {
+    return PNMAX == 32 ? (MODE ? 3 : 2)
+         : PNMAX == 64 ? (MODE ? 7 : 4)
+         : PNMAX == 96 ? (MODE ? 11 : 6)
+         : PNMAX == 128 ? (MODE ? 15 : 8)
+                        : (MODE ? 21 : 11);
+}
+
 template <int MODE, int PNMAX>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_m2l_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcArgs args) {
@@ -192,88 +203,103 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         return true;
     };
     if (warp == 0) {
-        if (lane == 0) {
-            // ---------------------------------------------------------------- producer
-            int j = 0;
-            for (int s = 0; s < 24 && ok; ++s) {
-                const int slot = s % args.nslab, use = s / args.nslab;
-                if (use >= 1 && !mbar_wait(&bar_sfree[slot], (use - 1) & 1, args.err, 16)) { ok = false; break; }
-                const int sg = s / 3, dz = s % 3 - 1;
+        // ---------------------------------------------------------------- producer (whole warp,
+        // one elected lane issues the copies)
+        int j = 0;
+        for (int s = 0; s < 24 && ok; ++s) {
+            const int slot = s % args.nslab, use = s / args.nslab;
+            if (use >= 1 && !mbar_wait_warp(&bar_sfree[slot], (use - 1) & 1, args.err, 16)) { ok = false; break; }
+            const int sg = s / 3, dz = s % 3 - 1;
+            unsigned char *dst = slabs + slot * slab_stride;
+            const int zc = sg * (half + 2) + (az + dz + 1);   // z plane index includes the zero plane below z = 0
+            if (elect_one()) {
                 mbar_arrive_expect_tx(&bar_sfull[slot], (uint32_t)(box_bytes * Md::ncomp));
-                unsigned char *dst = slabs + slot * slab_stride;
-                // z plane index includes the zero plane below z = 0
-                const int zc = sg * (half + 2) + (az + dz + 1);
                 // innermost coordinate in bytes: (ax0 - 1) * 16, a multiple of 16 (may be -16: zero fill)
                 tma_load_4d(dst, &map_hi, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
                 if (MODE == 2) tma_load_4d(dst + slab_bytes, &map_lo, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
-                for (int t9 = 0; t9 < 9 && ok; ++t9) {
-                    int olin;
-                    if (!op_of(s, t9 % 3 - 1, t9 / 3 - 1, olin)) continue;
-                    const int bslot = j % args.nbslots, buse = j / args.nbslots;
-                    if (buse >= 1 && !mbar_wait(&bar_bfree[bslot], (buse - 1) & 1, args.err, 16)) { ok = false; break; }
+            }
+            __syncwarp();
+            for (int t9 = 0; t9 < 9 && ok; ++t9) {
+                int olin;
+                if (!op_of(s, t9 % 3 - 1, t9 / 3 - 1, olin)) continue;
+                const int bslot = j % args.nbslots, buse = j / args.nbslots;
+                if (buse >= 1 && !mbar_wait_warp(&bar_bfree[bslot], (buse - 1) & 1, args.err, 16)) { ok = false; break; }
+                if (elect_one()) {
                     mbar_arrive_expect_tx(&bar_bfull[bslot], (uint32_t)bslot_bytes);
                     bulk_g2s(bring + bslot * bslot_bytes, args.B + (size_t)olin * bslot_bytes, (uint32_t)bslot_bytes,
                              &bar_bfull[bslot]);
-                    ++j;
                 }
+                __syncwarp();
+                ++j;
             }
-            // bounded drain of the last copies of every ring slot
-            for (int jj = (j - args.nbslots > 0 ? j - args.nbslots : 0); jj < j; ++jj)
-                mbar_wait(&bar_bfull[jj % args.nbslots], (jj / args.nbslots) & 1, args.err, 128);
-            for (int s = 24 - args.nslab; s < 24; ++s)
-                mbar_wait(&bar_sfull[s % args.nslab], (s / args.nslab) & 1, args.err, 128);
         }
-        __syncwarp();
+        // bounded drain of the last copies of every ring slot
+        for (int jj = (j - args.nbslots > 0 ? j - args.nbslots : 0); jj < j; ++jj)
+            mbar_wait_warp(&bar_bfull[jj % args.nbslots], (jj / args.nbslots) & 1, args.err, 128);
+        for (int s = 24 - args.nslab; s < 24; ++s)
+            mbar_wait_warp(&bar_sfull[s % args.nslab], (s / args.nslab) & 1, args.err, 128);
     } else if (warp == 1) {
-        if (lane == 0) {
-            // ---------------------------------------------------------------- MMA issuer
-            const uint32_t lboA = kSlabCells * 16, sboA = 160;
-            int j = 0;
-            for (int s = 0; s < 24 && ok; ++s) {
-                const int slot = s % args.nslab, use = s / args.nslab;
-                const int ab = s & 1;
-                if (s >= 2 && !mbar_wait(&bar_accfree[ab], ((s - 2) >> 1) & 1, args.err, 4)) { ok = false; break; }
-                if (!mbar_wait(&bar_sfull[slot], use & 1, args.err, 4)) { ok = false; break; }
-                tc_fence_after();
-                const uint32_t slab_a = smem_u32(slabs + slot * slab_stride);
-                const uint32_t acc_col = tacc + (uint32_t)(ab * args.pn);
-                uint32_t started = 0;
-                for (int t9 = 0; t9 < 9; ++t9) {
-                    int olin;
-                    const int dx = t9 % 3 - 1, dy = t9 / 3 - 1;
-                    if (!op_of(s, dx, dy, olin)) continue;
-                    const int bslot = j % args.nbslots;
-                    if (!mbar_wait(&bar_bfull[bslot], (j / args.nbslots) & 1, args.err, 8)) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t b_img = smem_u32(bring + bslot * bslot_bytes);
-                    const uint32_t a_view = slab_a + (uint32_t)(((dy + 1) * 10 + (dx + 1)) * 16);
-                    // one MMA per K-step; K-step 0 spans all Pn columns and initialises them
-                    for (int c = 0; c < args.nchunks; ++c) {
-                        const int2 cn = s_chunk[c];
-                        const uint32_t lboB = (uint32_t)(cn.x / 8) * 128u;
-                        const uint32_t idesc = instr_desc(Md::fmt, (uint32_t)cn.x);
-                        const uint32_t aoff = (uint32_t)c * 2u * lboA;
+        // ---------------------------------------------------------------- MMA issuer (whole warp,
+        // one elected lane issues; every per-K-step quantity is precomputed)
+        constexpr int kSteps = max_ksteps<MODE, PNMAX>();
+        const uint32_t lboA = kSlabCells * 16, sboA = 160;
+        uint32_t c_idesc[kSteps];
+        uint64_t c_bdesc[kSteps];          // B descriptor relative to the slot base
+        uint64_t c_adesc[kSteps];          // A descriptor relative to the view base
 #pragma unroll
-                        for (int pass = 0; pass < (MODE == 2 ? 3 : 1); ++pass) {
-                            const uint64_t ad = smem_desc(a_view + aoff + (pass == 2 ? (uint32_t)slab_bytes : 0u), lboA, sboA);
-                            const uint64_t bd = smem_desc(b_img + (uint32_t)cn.y + (pass == 1 ? (uint32_t)args.img_bytes : 0u),
-                                                          lboB, 128u);
-                            const uint32_t accum = (started || c > 0 || pass > 0) ? 1u : 0u;
-                            if (MODE == 0) mma_bf16(acc_col, ad, bd, idesc, accum);
-                            else mma_tf32(acc_col, ad, bd, idesc, accum);
+        for (int c = 0; c < kSteps; ++c) {
+            const int2 cn = s_chunk[c];
+            const int n = c < args.nchunks ? cn.x : 16;
+            c_idesc[c] = instr_desc(Md::fmt, (uint32_t)n);
+            c_bdesc[c] = smem_desc((uint32_t)cn.y, (uint32_t)(n / 8) * 128u, 128u);
+            c_adesc[c] = (uint64_t)(((uint32_t)c * 2u * lboA) >> 4);
+        }
+        const uint64_t a_lo = (uint64_t)((uint32_t)slab_bytes >> 4);      // A low part (TF32 x 3)
+        const uint64_t b_lo = (uint64_t)((uint32_t)args.img_bytes >> 4);  // B low part
+        const int nch = args.nchunks;
+        int j = 0;
+        for (int s = 0; s < 24 && ok; ++s) {
+            const int slot = s % args.nslab, use = s / args.nslab;
+            const int ab = s & 1;
+            if (s >= 2 && !mbar_wait_warp(&bar_accfree[ab], ((s - 2) >> 1) & 1, args.err, 4)) { ok = false; break; }
+            if (!mbar_wait_warp(&bar_sfull[slot], use & 1, args.err, 4)) { ok = false; break; }
+            tc_fence_after();
+            const uint32_t slab_a = smem_u32(slabs + slot * slab_stride);
+            const uint32_t acc_col = tacc + (uint32_t)(ab * args.pn);
+            uint32_t accum0 = 0;              // the step's first MMA initialises the buffer
+            for (int t9 = 0; t9 < 9; ++t9) {
+                int olin;
+                const int dx = t9 % 3 - 1, dy = t9 / 3 - 1;
+                if (!op_of(s, dx, dy, olin)) continue;
+                const int bslot = j % args.nbslots;
+                if (!mbar_wait_warp(&bar_bfull[bslot], (j / args.nbslots) & 1, args.err, 8)) { ok = false; break; }
+                tc_fence_after();
+                const uint64_t bbase = (uint64_t)(smem_u32(bring + bslot * bslot_bytes) >> 4);
+                const uint64_t abase = smem_desc(slab_a + (uint32_t)(((dy + 1) * 10 + (dx + 1)) * 16), lboA, sboA);
+#pragma unroll
+                for (int c = 0; c < kSteps; ++c) {
+                    const uint32_t on = c < nch ? 1u : 0u;
+                    const uint64_t ad = abase + c_adesc[c];
+                    const uint64_t bd = c_bdesc[c] + bbase;
+                    if (MODE == 0) {
+                        mma_bf16_elect(on, acc_col, ad, bd, c_idesc[c], accum0 | (uint32_t)c);
+                    } else {
+                        mma_tf32_elect(on, acc_col, ad, bd, c_idesc[c], accum0 | (uint32_t)c);
+                        if (MODE == 2) {
+                            mma_tf32_elect(on, acc_col, ad, bd + b_lo, c_idesc[c], 1u);
+                            mma_tf32_elect(on, acc_col, ad + a_lo, bd, c_idesc[c], 1u);
                         }
                     }
-                    started = 1;
-                    mma_commit(&bar_bfree[bslot]);
-                    ++j;
                 }
-                if (!ok) break;
-                mma_commit(&bar_sfree[slot]);
-                mma_commit(&bar_accfull[ab]);
+                accum0 = 1u;
+                mma_commit_elect(&bar_bfree[bslot]);
+                ++j;
             }
-            mma_commit(&bar_done);
+            if (!ok) break;
+            mma_commit_elect(&bar_sfree[slot]);
+            mma_commit_elect(&bar_accfull[ab]);
         }
-        __syncwarp();
+        mma_commit_elect(&bar_done);
     } else {
         // ---------------------------------------------------------------- accumulate / write
         const int q = warp & 3;                 // TMEM lane quarter of this warp
@@ -282,7 +308,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         for (int i = 0; i < PNMAX; ++i) acc[i] = 0.0f;
         for (int u = 0; u < 24 && ok; ++u) {
             const int ab = u & 1;
-            if (!mbar_wait(&bar_accfull[ab], (u >> 1) & 1, args.err, 32)) { ok = false; break; }
+            if (!mbar_wait_warp(&bar_accfull[ab], (u >> 1) & 1, args.err, 32)) { ok = false; break; }
             tc_fence_after();
 #pragma unroll
             for (int c0 = 0; c0 < PNMAX; c0 += 16) {
@@ -392,6 +418,12 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     int pn = 0, kfull = 0;
     plan_chunks(pl->D, pl->rho, pl->P, kg, ch, pn, kfull);
     if (pn > 176 || (int)ch.size() > kMaxChunks) return FC2T2_OK;
+    {
+        const int cls = pn <= 32 ? 32 : pn <= 64 ? 64 : pn <= 96 ? 96 : pn <= 128 ? 128 : 176;
+        const int cap = cls == 32 ? (mode ? 3 : 2) : cls == 64 ? (mode ? 7 : 4) : cls == 96 ? (mode ? 11 : 6)
+                      : cls == 128 ? (mode ? 15 : 8) : (mode ? 21 : 11);
+        if ((int)ch.size() > cap) return FC2T2_OK;   // cannot happen for orders <= 8; keep the CUDA-core M2L
+    }
     int off = 0;
     for (auto &c : ch) { c.b_off = off; off += c.N * c.K * esz; }
     const int img = off;
