@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--m2l", default="auto", choices=["auto", "tf32x3", "tf32", "bf16", "fp32"])
+    ap.add_argument("--m2l", default="auto", choices=["auto", "tf32x3", "bf16x3", "tf32", "bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
@@ -323,8 +323,8 @@ def roofline_for(m: Measured, peaks):
     basis = "measured bf16 sustained (MEASURED_PEAKS.json)"
     if bf16 is None:
         bf16, basis = 1700.0, "fallback bf16 sustained"
-    peak = bf16 if m.mode == "bf16" else bf16 * TF32_PER_BF16
-    if m.mode != "bf16":
+    peak = bf16 if m.mode in ("bf16", "bf16x3") else bf16 * TF32_PER_BF16
+    if m.mode not in ("bf16", "bf16x3"):
         basis += " x nominal TF32/BF16 ratio 1.1/2.25"
     achieved = issued / (m2l_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,

@@ -75,8 +75,10 @@ typedef enum {
     FC2T2_M2L_FP32 = 0,          /* FP32 on the CUDA cores */
     FC2T2_M2L_TF32 = 1,          /* tcgen05 tensor cores, TF32 operands, FP32 accumulation */
     FC2T2_M2L_BF16 = 2,          /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
-    FC2T2_M2L_TF32X3 = 3         /* tcgen05, each operand split into TF32 high + low parts,
+    FC2T2_M2L_TF32X3 = 3,        /* tcgen05, each operand split into TF32 high + low parts,
                                     three products (hi*hi + hi*lo + lo*hi): FP32 accuracy */
+    FC2T2_M2L_BF16X3 = 4         /* as TF32X3 with BF16 parts (~16 significant bits per operand,
+                                    half the MMA instructions): within the FP32 error bar */
 } fc2t2_m2l_prec;
 
 typedef struct fc2t2_plan_s *fc2t2_plan;

@@ -270,7 +270,7 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     }
     if (d->channels != 1) return set_error(FC2T2_ERR_UNSUPPORTED, "only channels == 1 is supported");
     if (d->m2l != FC2T2_M2L_FP32 && d->m2l != FC2T2_M2L_TF32 && d->m2l != FC2T2_M2L_BF16 &&
-        d->m2l != FC2T2_M2L_TF32X3)
+        d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3)
         return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
     if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||
         d->max_queries > (int64_t)INT32_MAX)
@@ -347,15 +347,19 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
         for (int l = 0; l + 1 < pl->nlev; ++l)
             if ((st = check_cuda(launch_m2m(pl, s, l), "m2m")) != FC2T2_OK) return st;
     }
-    for (int l = pl->nlev - 1; l >= 0; --l) {
-        {
-            StageScope scope(pl, s, FC2T2_STAGE_M2L);
-            if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
-        }
-        if (l + 1 < pl->nlev) {
-            StageScope scope(pl, s, FC2T2_STAGE_L2L);
-            if ((st = check_cuda(launch_l2l(pl, s, l), "l2l")) != FC2T2_OK) return st;
-        }
+    // M2L of every level (independent given the moments): the tensor-core levels in one launch,
+    // the others on the CUDA cores; then L2L from the coarsest level down
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_M2L);
+        if (pl->tc.enabled && (st = check_cuda(launch_m2l_tc_all(pl, s), "m2l (tensor cores)")) != FC2T2_OK)
+            return st;
+        for (int l = pl->nlev - 1; l >= 0; --l)
+            if (!(pl->tc.enabled && pl->tc.level_ok[l]))
+                if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
+    }
+    for (int l = pl->nlev - 2; l >= 0; --l) {
+        StageScope scope(pl, s, FC2T2_STAGE_L2L);
+        if ((st = check_cuda(launch_l2l(pl, s, l), "l2l")) != FC2T2_OK) return st;
     }
     return FC2T2_OK;
 }

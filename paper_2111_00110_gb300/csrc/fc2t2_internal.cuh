@@ -149,7 +149,7 @@ cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w);
-cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s);
 // register-resident M2M / L2L for orders <= 6 (return false when not applicable)
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);
 bool launch_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);

@@ -21,8 +21,9 @@
 // MMA instruction costs at least ~40 cycles whatever its size and runs at full rate only from
 // N ~ 96, so one instruction per K-step is cheaper than splitting k into narrow chunks.)
 //
-// Precision: BF16 or TF32 operands with FP32 accumulation, or TF32 x 3 (A_hi B_hi + A_hi B_lo
-// + A_lo B_hi, the low parts being the TF32 rounding residues), accurate to FP32.  The tensor
+// Precision: BF16 or TF32 operands with FP32 accumulation, or a split form (A_hi B_hi + A_hi B_lo
+// + A_lo B_hi, the low parts being the rounding residues) in TF32 x 3 or BF16 x 3; both split
+// forms are within the FP32 bar (1e-5 relative L2), BF16 x 3 with half the MMAs of TF32 x 3.  The tensor
 // core's accumulation over thousands of MMAs loses low bits, so each step's partial sum is
 // accumulated in its own TMEM buffer (two, alternating) and added into FP32 registers.
 //
@@ -54,13 +55,26 @@ struct TcChunk {
     int k0;
 };
 
-struct TcArgs {
-    float *L;
-    const unsigned char *B;       // operator images of this level: [343][ncomp][img_bytes]
-    int *err;
-    int nl;                       // cells per dimension at this level
-    int Pp;
+struct TcLevel {
+    float *L;                     // this level's local coefficients
+    const unsigned char *B;       // this level's operator images: [343][ncomp][img_bytes]
+    int nl;                       // cells per dimension
     int finest;                   // 1: no hole
+    int tiles_x, tiles_y;         // tiles per parity class along x, y (z: n/2)
+    int block0;                   // first block of this level in the launch
+};
+
+struct TcMaps {
+    CUtensorMap m[kMaxLevels][2];   // packed-moment descriptors (high, low part) per level
+};
+
+// All levels' M2L run in one launch (they are independent given the moments); blocks are
+// ordered finest level first so the small coarse levels fill the tail of the last wave.
+struct TcArgs {
+    TcLevel lv[kMaxLevels];
+    int nlev;
+    int *err;
+    int Pp;
     int nkc;                      // 16-byte chunks per slab row
     int img_bytes;                // one operator image (one component)
     int ncomp_b;                  // 1, or 2 for TF32 x 3 (hi, lo)
@@ -70,16 +84,17 @@ struct TcArgs {
     uint32_t tmem_cols;
     int nslab;                    // slab ring slots
     int nbslots;                  // operator ring slots
-    int tiles_x, tiles_y;         // tiles per parity class along x, y (z: half)
 };
 
-template <int MODE>   // 0: BF16, 1: TF32, 2: TF32 x 3
+template <int MODE>   // 0: BF16, 1: TF32, 2: TF32 x 3, 3: BF16 x 3
 struct TcMode {
-    static constexpr int esz = MODE == 0 ? 2 : 4;
+    static constexpr bool bf16 = MODE == 0 || MODE == 3;
+    static constexpr bool split = MODE == 2 || MODE == 3;   // high + low parts, three products
+    static constexpr int esz = bf16 ? 2 : 4;
     static constexpr int epc = 16 / esz;          // elements per 16-byte chunk
     static constexpr int eps = 32 / esz;          // elements per MMA K-step
-    static constexpr int ncomp = MODE == 2 ? 2 : 1;
-    static constexpr uint32_t fmt = MODE == 0 ? 1u : 2u;
+    static constexpr int ncomp = split ? 2 : 1;
+    static constexpr uint32_t fmt = bf16 ? 1u : 2u;
 };
 
 __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
@@ -122,9 +137,16 @@ __global__ void __launch_bounds__(256) k_pack_tc(const float *__restrict__ M, un
             }
         const int64_t o = ((((int64_t)sg * (half + 2) + (z + 1)) * nkc + kc) * half + y) * half + x;
         uint4 *dst = reinterpret_cast<uint4 *>(out + o * 16);
-        if (MODE == 0) {
-            *dst = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
-                              pack_bf16x2(v[6], v[7]));
+        if (Md::bf16) {
+            float h[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e) h[e] = round_bf16(v[e]);
+            *dst = make_uint4(pack_bf16x2(h[0], h[1]), pack_bf16x2(h[2], h[3]), pack_bf16x2(h[4], h[5]),
+                              pack_bf16x2(h[6], h[7]));
+            if (MODE == 3)
+                *reinterpret_cast<uint4 *>(out + comp_stride + o * 16) =
+                    make_uint4(pack_bf16x2(v[0] - h[0], v[1] - h[1]), pack_bf16x2(v[2] - h[2], v[3] - h[3]),
+                               pack_bf16x2(v[4] - h[4], v[5] - h[5]), pack_bf16x2(v[6] - h[6], v[7] - h[7]));
         } else {
             float h[4];
 #pragma unroll
@@ -143,16 +165,17 @@ __global__ void __launch_bounds__(256) k_pack_tc(const float *__restrict__ M, un
 // TF32: 8); the issue loop is unrolled to it and predicates off the steps a plan does not use
 template <int MODE, int PNMAX>
 constexpr int max_ksteps() {
-    return PNMAX == 32 ? (MODE ? 3 : 2)
-         : PNMAX == 64 ? (MODE ? 7 : 4)
-         : PNMAX == 96 ? (MODE ? 11 : 6)
-         : PNMAX == 128 ? (MODE ? 15 : 8)
-                        : (MODE ? 21 : 11);
+    constexpr bool tf = !TcMode<MODE>::bf16;
+    return PNMAX == 32 ? (tf ? 3 : 2)
+         : PNMAX == 64 ? (tf ? 7 : 4)
+         : PNMAX == 96 ? (tf ? 11 : 6)
+         : PNMAX == 128 ? (tf ? 15 : 8)
+                        : (tf ? 21 : 11);
 }
 
 template <int MODE, int PNMAX>
 __global__ void __launch_bounds__(kTcThreads, 1)
-    k_m2l_tc(const __grid_constant__ CUtensorMap map_hi, const __grid_constant__ CUtensorMap map_lo, const TcArgs args) {
+    k_m2l_tc(const __grid_constant__ TcMaps maps, const TcArgs args) {
     using Md = TcMode<MODE>;
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t bar_bfull[kMaxBSlots], bar_bfree[kMaxBSlots], bar_sfull[kMaxSlabSlots], bar_sfree[kMaxSlabSlots];
@@ -161,14 +184,22 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     __shared__ int2 s_chunk[kMaxChunks];         // (N, b_off) of each K-step
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int half = args.nl >> 1;
-    const int tiles_per_class = args.tiles_x * args.tiles_y * half;
-    const int pi = blockIdx.x / tiles_per_class;
-    int tr = blockIdx.x % tiles_per_class;
-    const int tx = tr % args.tiles_x;
-    tr /= args.tiles_x;
-    const int ty = tr % args.tiles_y;
-    const int az = tr / args.tiles_y;
+    int lvl = 0;
+#pragma unroll
+    for (int i = 1; i < kMaxLevels; ++i)
+        if (i < args.nlev && (int)blockIdx.x >= args.lv[i].block0) lvl = i;
+    const TcLevel lv = args.lv[lvl];
+    const CUtensorMap *map_hi = &maps.m[lvl][0];
+    const CUtensorMap *map_lo = &maps.m[lvl][1];
+    const int half = lv.nl >> 1;
+    const int tiles_per_class = lv.tiles_x * lv.tiles_y * half;
+    const int bl = (int)blockIdx.x - lv.block0;
+    const int pi = bl / tiles_per_class;
+    int tr = bl % tiles_per_class;
+    const int tx = tr % lv.tiles_x;
+    tr /= lv.tiles_x;
+    const int ty = tr % lv.tiles_y;
+    const int az = tr / lv.tiles_y;
     const int ax0 = tx * 8, ay0 = ty * 16;
     const int pix = pi & 1, piy = (pi >> 1) & 1, piz = (pi >> 2) & 1;
 
@@ -198,7 +229,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     auto op_of = [&](int s, int dx, int dy, int &olin) -> bool {
         const int sg = s / 3, dz = s % 3 - 1;
         const int ox = 2 * dx + (sg & 1) - pix, oy = 2 * dy + ((sg >> 1) & 1) - piy, oz = 2 * dz + (sg >> 2) - piz;
-        if (!args.finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return false;
+        if (!lv.finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) return false;
         olin = (ox + 3) + 7 * (oy + 3) + 49 * (oz + 3);
         return true;
     };
@@ -215,8 +246,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (elect_one()) {
                 mbar_arrive_expect_tx(&bar_sfull[slot], (uint32_t)(box_bytes * Md::ncomp));
                 // innermost coordinate in bytes: (ax0 - 1) * 16, a multiple of 16 (may be -16: zero fill)
-                tma_load_4d(dst, &map_hi, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
-                if (MODE == 2) tma_load_4d(dst + slab_bytes, &map_lo, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                tma_load_4d(dst, map_hi, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
+                if (Md::split) tma_load_4d(dst + slab_bytes, map_lo, (ax0 - 1) * 16, ay0 - 1, 0, zc, &bar_sfull[slot]);
             }
             __syncwarp();
             for (int t9 = 0; t9 < 9 && ok; ++t9) {
@@ -226,7 +257,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 if (buse >= 1 && !mbar_wait_warp(&bar_bfree[bslot], (buse - 1) & 1, args.err, 16)) { ok = false; break; }
                 if (elect_one()) {
                     mbar_arrive_expect_tx(&bar_bfull[bslot], (uint32_t)bslot_bytes);
-                    bulk_g2s(bring + bslot * bslot_bytes, args.B + (size_t)olin * bslot_bytes, (uint32_t)bslot_bytes,
+                    bulk_g2s(bring + bslot * bslot_bytes, lv.B + (size_t)olin * bslot_bytes, (uint32_t)bslot_bytes,
                              &bar_bfull[bslot]);
                 }
                 __syncwarp();
@@ -281,8 +312,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     const uint32_t on = c < nch ? 1u : 0u;
                     const uint64_t ad = abase + c_adesc[c];
                     const uint64_t bd = c_bdesc[c] + bbase;
-                    if (MODE == 0) {
+                    if (Md::bf16) {
                         mma_bf16_elect(on, acc_col, ad, bd, c_idesc[c], accum0 | (uint32_t)c);
+                        if (MODE == 3) {
+                            mma_bf16_elect(on, acc_col, ad, bd + b_lo, c_idesc[c], 1u);
+                            mma_bf16_elect(on, acc_col, ad + a_lo, bd, c_idesc[c], 1u);
+                        }
                     } else {
                         mma_tf32_elect(on, acc_col, ad, bd, c_idesc[c], accum0 | (uint32_t)c);
                         if (MODE == 2) {
@@ -327,8 +362,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const int x = ax0 + (r & 7), y = ay0 + (r >> 3);
             if (x < half && y < half) {
                 const int64_t t = (int64_t)(2 * x + pix) +
-                                  (int64_t)args.nl * ((2 * y + piy) + (int64_t)args.nl * (2 * az + piz));
-                float *Lrow = args.L + t * args.Pp;
+                                  (int64_t)lv.nl * ((2 * y + piy) + (int64_t)lv.nl * (2 * az + piz));
+                float *Lrow = lv.L + t * args.Pp;
 #pragma unroll
                 for (int e = 0; e < PNMAX; e += 4)
                     if (e + 4 <= args.Pp)
@@ -412,22 +447,25 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
     pl->tc.enabled = 0;
     if (pl->D != 3) return FC2T2_OK;
-    const int mode = pl->desc.m2l == FC2T2_M2L_BF16 ? 0 : (pl->desc.m2l == FC2T2_M2L_TF32 ? 1 : 2);
-    const int esz = mode == 0 ? 2 : 4, epc = 16 / esz, kg = 32 / esz;
+    const int mode = pl->desc.m2l == FC2T2_M2L_BF16 ? 0 : pl->desc.m2l == FC2T2_M2L_TF32 ? 1
+                   : pl->desc.m2l == FC2T2_M2L_TF32X3 ? 2 : 3;
+    const bool bf16 = mode == 0 || mode == 3, split = mode == 2 || mode == 3;
+    const int esz = bf16 ? 2 : 4, epc = 16 / esz, kg = 32 / esz;
     std::vector<TcChunk> ch;
     int pn = 0, kfull = 0;
     plan_chunks(pl->D, pl->rho, pl->P, kg, ch, pn, kfull);
     if (pn > 176 || (int)ch.size() > kMaxChunks) return FC2T2_OK;
     {
         const int cls = pn <= 32 ? 32 : pn <= 64 ? 64 : pn <= 96 ? 96 : pn <= 128 ? 128 : 176;
-        const int cap = cls == 32 ? (mode ? 3 : 2) : cls == 64 ? (mode ? 7 : 4) : cls == 96 ? (mode ? 11 : 6)
-                      : cls == 128 ? (mode ? 15 : 8) : (mode ? 21 : 11);
+        const bool tf = !bf16;
+        const int cap = cls == 32 ? (tf ? 3 : 2) : cls == 64 ? (tf ? 7 : 4) : cls == 96 ? (tf ? 11 : 6)
+                      : cls == 128 ? (tf ? 15 : 8) : (tf ? 21 : 11);
         if ((int)ch.size() > cap) return FC2T2_OK;   // cannot happen for orders <= 8; keep the CUDA-core M2L
     }
     int off = 0;
     for (auto &c : ch) { c.b_off = off; off += c.N * c.K * esz; }
     const int img = off;
-    const int ncomp = mode == 2 ? 2 : 1;
+    const int ncomp = split ? 2 : 1;
     const int nofs = 343;
     const int nkc = kfull * esz / 16;
     // shared memory: slab ring + operator ring (two CTAs per SM when both fit in half of it)
@@ -474,9 +512,16 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
                         }
                         const size_t pos = (size_t)c.b_off + ((size_t)(k / epc) * (c.N / 8) + n / 8) * 128 +
                                            (n % 8) * 16 + (k % epc) * esz;
-                        if (mode == 0) {
+                        if (bf16) {
                             const uint16_t h = to_bf16((float)v);
                             std::memcpy(base + pos, &h, 2);
+                            if (mode == 3) {
+                                float hf;
+                                const uint32_t u = (uint32_t)h << 16;
+                                std::memcpy(&hf, &u, 4);
+                                const uint16_t lo = to_bf16((float)(v - (double)hf));
+                                std::memcpy(base + img + pos, &lo, 2);
+                            }
                         } else {
                             const float hi = to_tf32((float)v);
                             std::memcpy(base + pos, &hi, 4);
@@ -542,7 +587,7 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     pl->tc.tmem_cols = cols <= 32 ? 32 : (cols <= 64 ? 64 : (cols <= 128 ? 128 : (cols <= 256 ? 256 : 512)));
     // MMA work issued per transform (2 x multiply-adds), for roofline reporting
     double per_op = 0.0;
-    for (const TcChunk &c : ch) per_op += 2.0 * 128 * c.N * c.K * (mode == 2 ? 3 : 1);
+    for (const TcChunk &c : ch) per_op += 2.0 * 128 * c.N * c.K * (split ? 3 : 1);
     double total = 0.0;
     for (int l = 0; l < pl->nlev; ++l) {
         const int half = pl->lev[l].n >> 1;
@@ -555,31 +600,48 @@ fc2t2_status build_tc_operators(fc2t2_plan_s *pl, const std::vector<double> &dta
     return FC2T2_OK;
 }
 
-cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
-    const Level &lv = pl->lev[level];
-    const int half = lv.n >> 1;
+// Pack every tensor-core level's moments, then run all those levels' M2L in one launch.
+cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s) {
     const int nkc = pl->tc.kbytes / 16;
-    // pack this level's moments into the tensor-core layout
-    {
-        const int64_t total = (int64_t)8 * half * half * half * nkc;
-        const int64_t want = (total + 255) / 256;
-        const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
-        const float *M = pl->d_M + lv.off * pl->Pp;
-        unsigned char *out = static_cast<unsigned char *>(pl->tc.packed[level]);
-        pl->launches[FC2T2_STAGE_M2L] += 1;
-        if (pl->tc.mode == 0) k_pack_tc<0><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
-        else if (pl->tc.mode == 1) k_pack_tc<1><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
-        else k_pack_tc<2><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
     TcArgs a;
-    a.L = pl->d_L + lv.off * pl->Pp;
-    a.B = static_cast<const unsigned char *>(pl->d_mma_ops) + (size_t)level * 343 * pl->tc.ncomp * pl->tc.img_bytes;
+    TcMaps maps;          // descriptors, copied into the launch parameters
+    std::memset(&a, 0, sizeof(a));
+    int nl_used = 0, block = 0;
+    for (int level = 0; level < pl->nlev; ++level) {
+        if (!pl->tc.level_ok[level]) continue;
+        const Level &lv = pl->lev[level];
+        const int half = lv.n >> 1;
+        {
+            const int64_t total = (int64_t)8 * half * half * half * nkc;
+            const int64_t want = (total + 255) / 256;
+            const unsigned blocks = (unsigned)(want < 152 * 16 ? want : 152 * 16);
+            const float *M = pl->d_M + lv.off * pl->Pp;
+            unsigned char *out = static_cast<unsigned char *>(pl->tc.packed[level]);
+            pl->launches[FC2T2_STAGE_M2L] += 1;
+            if (pl->tc.mode == 0) k_pack_tc<0><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+            else if (pl->tc.mode == 1) k_pack_tc<1><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+            else if (pl->tc.mode == 2) k_pack_tc<2><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+            else k_pack_tc<3><<<blocks, 256, 0, s>>>(M, out, lv.n, pl->Pp, nkc);
+            const cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        TcLevel &t = a.lv[nl_used];
+        t.L = pl->d_L + lv.off * pl->Pp;
+        t.B = static_cast<const unsigned char *>(pl->d_mma_ops) + (size_t)level * 343 * pl->tc.ncomp * pl->tc.img_bytes;
+        t.nl = lv.n;
+        t.finest = level == 0 ? 1 : 0;
+        t.tiles_x = (half + 7) / 8;
+        t.tiles_y = (half + 15) / 16;
+        t.block0 = block;
+        std::memcpy(&maps.m[nl_used][0], &pl->tc.maps[level][0], sizeof(CUtensorMap));
+        std::memcpy(&maps.m[nl_used][1], &pl->tc.maps[level][1], sizeof(CUtensorMap));
+        block += 8 * t.tiles_x * t.tiles_y * half;
+        ++nl_used;
+    }
+    if (nl_used == 0) return cudaSuccess;
+    a.nlev = nl_used;
     a.err = pl->d_flags + 1;
-    a.nl = lv.n;
     a.Pp = pl->Pp;
-    a.finest = level == 0 ? 1 : 0;
     a.nkc = nkc;
     a.img_bytes = pl->tc.img_bytes;
     a.ncomp_b = pl->tc.ncomp;
@@ -591,22 +653,19 @@ cudaError_t launch_m2l_tc(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     a.tmem_cols = (uint32_t)pl->tc.tmem_cols;
     a.nslab = pl->tc.nbuf;
     a.nbslots = pl->tc.nbslots;
-    a.tiles_x = (half + 7) / 8;
-    a.tiles_y = (half + 15) / 16;
-    const unsigned blocks = (unsigned)(8 * a.tiles_x * a.tiles_y * half);
-    const CUtensorMap &mh = *reinterpret_cast<const CUtensorMap *>(&pl->tc.maps[level][0]);
-    const CUtensorMap &ml = *reinterpret_cast<const CUtensorMap *>(&pl->tc.maps[level][1]);
+    const unsigned blocks = (unsigned)block;
     pl->launches[FC2T2_STAGE_M2L] += 1;
     const int key = pl->tc.mode * 8 + (a.pn <= 32 ? 0 : a.pn <= 64 ? 1 : a.pn <= 96 ? 2 : a.pn <= 128 ? 3 : 4);
 #define FC2T2_TC_CASE(MODE_, IDX_, PN_)                                                                   \
     case (MODE_) * 8 + (IDX_):                                                                           \
         cudaFuncSetAttribute(k_m2l_tc<MODE_, PN_>, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->tc.smem); \
-        k_m2l_tc<MODE_, PN_><<<blocks, kTcThreads, pl->tc.smem, s>>>(mh, ml, a);                          \
+        k_m2l_tc<MODE_, PN_><<<blocks, kTcThreads, pl->tc.smem, s>>>(maps, a);                            \
         break;
     switch (key) {
         FC2T2_TC_CASE(0, 0, 32) FC2T2_TC_CASE(0, 1, 64) FC2T2_TC_CASE(0, 2, 96) FC2T2_TC_CASE(0, 3, 128) FC2T2_TC_CASE(0, 4, 176)
         FC2T2_TC_CASE(1, 0, 32) FC2T2_TC_CASE(1, 1, 64) FC2T2_TC_CASE(1, 2, 96) FC2T2_TC_CASE(1, 3, 128) FC2T2_TC_CASE(1, 4, 176)
         FC2T2_TC_CASE(2, 0, 32) FC2T2_TC_CASE(2, 1, 64) FC2T2_TC_CASE(2, 2, 96) FC2T2_TC_CASE(2, 3, 128) FC2T2_TC_CASE(2, 4, 176)
+        FC2T2_TC_CASE(3, 0, 32) FC2T2_TC_CASE(3, 1, 64) FC2T2_TC_CASE(3, 2, 96) FC2T2_TC_CASE(3, 3, 128) FC2T2_TC_CASE(3, 4, 176)
         default: return cudaErrorInvalidValue;
     }
 #undef FC2T2_TC_CASE

@@ -4,8 +4,8 @@
 // Shared-memory matrix descriptors use the canonical K-major layout without swizzling:
 // a "core matrix" is 8 rows x 16 bytes stored contiguously (row r at +16 r); core matrices
 // adjacent along K are `lbo` bytes apart, core matrices adjacent along M/N are `sbo` bytes
-// apart.  Every wait is bounded: on timeout it records a code in a device error word and
-// returns false, so no kernel can spin forever.
+// apart.  Every wait is bounded in time (0.2 s of the global timer): on timeout it records a
+// code in a device error word and returns false, so no kernel can spin forever.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -14,7 +14,13 @@
 namespace fc2t2 {
 namespace tc {
 
-constexpr uint32_t kSpinLimit = 1u << 22;   // ~0.1-1 s of polling, far above any legal wait
+constexpr uint64_t kWaitLimitNs = 200ull * 1000 * 1000;   // 0.2 s: far above any legal wait
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -43,10 +49,15 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity to complete.
+// Bounded wait for the phase with the given parity to complete (gives up after kWaitLimitNs).
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (mbar_try_wait(bar, parity)) return true;
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > kWaitLimitNs) break;
+    }
     atomicOr(err, code);
     return false;
 }
@@ -188,8 +199,13 @@ __device__ __forceinline__ bool elect_one() {
 }
 // Warp-uniform bounded wait: every lane polls, the warp leaves together.
 __device__ __forceinline__ bool mbar_wait_warp(uint64_t *bar, uint32_t parity, int *err, int code) {
-    for (uint32_t it = 0; it < kSpinLimit; ++it)
-        if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (__all_sync(0xffffffffu, mbar_try_wait(bar, parity))) return true;
+        if (__any_sync(0xffffffffu, globaltimer_ns() - t0 > kWaitLimitNs)) break;
+    }
     if ((threadIdx.x & 31) == 0) atomicOr(err, code);
     return false;
 }
@@ -205,6 +221,9 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<uint32_t *>(&v);
+}
+__device__ __forceinline__ float round_bf16(float x) {
+    return __bfloat162float(__float2bfloat16_rn(x));
 }
 __device__ __forceinline__ float round_tf32(float x) {
     uint32_t r;

@@ -296,7 +296,6 @@ cudaError_t launch_m2l_simple(const fc2t2_plan_s *pl, cudaStream_t s, int level)
 }
 
 cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
-    if (pl->tc.enabled && pl->tc.level_ok[level]) return launch_m2l_tc(pl, s, level);
     return launch_m2l_simple(pl, s, level);
 }
 

@@ -250,10 +250,10 @@ def test_uniform3d_full_size_forward_backward(lib):
 # ----------------------------------------------------------------- tensor-core M2L (3D)
 
 # rel-L2 bars: TF32 x 3 is FP32-accurate; single-pass TF32 / BF16 are the mixed forms
-TC_BARS = {"tf32x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2), "bf16": (1e-2, 5e-2)}
+TC_BARS = {"tf32x3": (1e-5, 1e-4), "bf16x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2), "bf16": (1e-2, 5e-2)}
 
 
-@pytest.mark.parametrize("mode", ["tf32x3", "tf32", "bf16"])
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32", "bf16"])
 @pytest.mark.parametrize("grid,order", [(16, 4), (16, 6), (32, 6), (8, 3)])
 def test_tensor_core_m2l_forward(lib, mode, grid, order):
     wl = workloads.uniform(500 + grid + order, 3, 6000, 5000, grid, order, 1.3 / grid)
@@ -265,7 +265,7 @@ def test_tensor_core_m2l_forward(lib, mode, grid, order):
     assert_close(y, yo, rel=rel, elem=elem, what=f"{mode} n{grid} rho{order}")
 
 
-@pytest.mark.parametrize("mode", ["tf32x3", "tf32"])
+@pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32"])
 def test_tensor_core_m2l_backward(lib, mode):
     wl = workloads.uniform(777, 3, 4000, 3500, 16, 6, 0.08)
     ybar = wl.ybar()
