@@ -9,10 +9,11 @@ oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--m2l MODE]
 
-MODE "auto" (default) reports the FP32-accurate path (M2L on tcgen05 with TF32 x 3 operands) as
-`value`, and the mixed-precision form (single TF32 M2L) and the plain CUDA-core FP32 form as
-`variants`, each with its measured error against the oracle on a seeded sample (4096 queries for
-y, 4096 sources for wbar and pbar with a fixed seeded cotangent).
+MODE "auto" (default) reports the FP32-accurate path (M2L on tcgen05 with BF16 x 3 split operands)
+as `value`, and as `variants` the other FP32-accurate split (TF32 x 3), the mixed-precision forms
+(single-pass TF32 and BF16 M2L) and the plain CUDA-core FP32 form, each with its measured error
+against the oracle on a seeded sample (4096 queries for y, 4096 sources for wbar and pbar with a
+fixed seeded cotangent).
 
 Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle on the host cores
 on a bounded sample of the same workload (the queries -- and, for the backward, the sources --
@@ -308,29 +309,36 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
 
 
 def roofline_for(m: Measured, peaks):
-    """Roofline of the dominant kernel (M2L) for one measured form."""
+    """Roofline of the dominant kernel (the M2L contraction) for one measured form.
+
+    `achieved` counts ALGORITHMIC flops: 2 x (number of |b| + |k| <= order coefficient products)
+    per interacting cell pair, summed over the interaction lists of every level, two transforms
+    per step.  On the tensor cores the kernel executes more than that (dense MMA tiles over the
+    degree triangle, and three products per split form); `executed` reports those flops and the
+    tensor-pipe fraction they reach.  Time = the M2L stage's CUDA events on the launching stream
+    (the operand pack pass is a separate stage)."""
     m2l_ms = m.stage_ms["m2l"]                       # per step = two transforms
     useful = 2 * m.info["m2l_useful_flops"]
     issued = 2 * m.info["m2l_issued_flops"]
+    achieved = useful / (m2l_ms / 1e3) / 1e12
     if m.mode == "fp32":
         sm = peaks.get("sm_max_mhz", 2070.0)
         peak = fp32_peak_tflops(sm)
-        achieved = useful / (m2l_ms / 1e3) / 1e12
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": None, "kernel": "m2l (CUDA cores, FP32)", "flops_per_step": useful,
                 "peak_basis": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm:.0f} MHz"}
     bf16 = peaks.get("bf16_tflops_sustained")
-    basis = "measured bf16 sustained (MEASURED_PEAKS.json)"
+    basis = "of measured bf16 sustained (MEASURED_PEAKS.json)"
     if bf16 is None:
-        bf16, basis = 1700.0, "fallback bf16 sustained"
+        bf16, basis = 1700.0, "of fallback bf16 sustained"
     peak = bf16 if m.mode in ("bf16", "bf16x3") else bf16 * TF32_PER_BF16
     if m.mode not in ("bf16", "bf16x3"):
         basis += " x nominal TF32/BF16 ratio 1.1/2.25"
-    achieved = issued / (m2l_ms / 1e3) / 1e12
+    executed = issued / (m2l_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"m2l (tcgen05, {m.mode}) incl. its pack pass",
-            "flops_per_step": issued, "useful_flops_per_step": useful,
-            "useful_achieved": useful / (m2l_ms / 1e3) / 1e12, "peak_basis": basis}
+            "traffic": None, "kernel": f"k_m2l_tc (tcgen05, {m.mode})", "flops_per_step": useful,
+            "executed": {"flops_per_step": issued, "achieved": executed, "frac": executed / peak},
+            "peak_basis": basis}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -348,11 +356,11 @@ def run_ours(args, rank, world, local_rank):
     ref = None
     if not args.no_check and rank == 0:
         ref = oracle_reference_sample(wl)
-    primary = "tf32x3" if args.m2l == "auto" else args.m2l
+    primary = "bf16x3" if args.m2l == "auto" else args.m2l
     main = measure_mode(primary, wl, args, world, dev, flush, ref=ref, do_e2e=not args.no_e2e, clocks=True)
     variants = {}
     if args.m2l == "auto":
-        for mode in ("tf32", "fp32"):
+        for mode in ("tf32x3", "tf32", "bf16", "fp32"):
             variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref)
     if rank != 0:
         return

@@ -132,6 +132,14 @@ FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
                             const float *q, int64_t M, const float *ybar,
                             float *wbar, float *pbar);
 
+/* Synchronise `stream` and report the device-side conditions raised on `plan`: TIMEOUT if a
+ * bounded device-side wait of the tensor-core M2L gave up in any call since the last check (the
+ * outputs of that call are then incomplete; the condition is cleared by this check), DOMAIN if
+ * check_domain is set and the last call saw a point outside the domain.  Forward and backward
+ * make the same check themselves when check_domain is set.  Errors: INVALID_ARG, CUDA, and the
+ * two conditions above. */
+FC2T2_API fc2t2_status fc2t2_plan_check(fc2t2_plan plan, void *stream);
+
 /* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
  * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,
  * each of n_inst entries) with N[i] sources and M[i] queries.  All instances are enqueued on
@@ -157,6 +165,8 @@ typedef struct {
     double m2l_issued_flops;     /* multiply-add work (x2) the M2L kernels issue, incl. the zeros
                                     inside the dense tensor-core blocks; = useful on CUDA cores */
     int64_t device_bytes;        /* device memory owned by the plan */
+    int m2l_classes_per_cta;     /* target parity classes one tensor-core CTA accumulates (1, 2 or
+                                    4; 0 when the M2L runs on the CUDA cores) */
 } fc2t2_plan_info;
 
 /* Fill *info for `plan`.  Errors: INVALID_ARG (NULL argument). */
@@ -170,7 +180,8 @@ typedef enum {
     FC2T2_STAGE_M2L = 3,
     FC2T2_STAGE_L2L = 4,
     FC2T2_STAGE_L2P = 5,         /* L2P, and the L2P gradient of the backward pass */
-    FC2T2_NUM_STAGES = 6
+    FC2T2_STAGE_M2L_PACK = 6,    /* rewrite of the moments into the tensor-core operand layout */
+    FC2T2_NUM_STAGES = 7
 } fc2t2_stage;
 
 /* Diagnostics, not part of the transform: while enabled, every call on `plan` records CUDA

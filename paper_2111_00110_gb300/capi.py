@@ -40,8 +40,9 @@ EXPORTS = (
     "fc2t2_forward_batched",
     "fc2t2_backward_batched",
     "fc2t2_plan_query",
+    "fc2t2_plan_check",
 )
-STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p")
+STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack")
 
 
 class PlanDesc(ctypes.Structure):
@@ -72,6 +73,7 @@ class PlanInfo(ctypes.Structure):
         ("m2l_useful_flops", ctypes.c_double),
         ("m2l_issued_flops", ctypes.c_double),
         ("device_bytes", ctypes.c_int64),
+        ("m2l_classes_per_cta", ctypes.c_int),
     ]
 
 
@@ -109,6 +111,7 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_forward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fc2t2_backward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fc2t2_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
+        lib.fc2t2_plan_check.argtypes = [vp, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
@@ -143,6 +146,11 @@ def forward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, y: i
 def backward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int,
              wbar: int, pbar: int) -> None:
     check(load().fc2t2_backward(plan, stream, p, w, N, q, M, ybar, wbar, pbar))
+
+
+def plan_check(plan: int, stream: int) -> None:
+    """Synchronise the stream; raise on a device-side timeout or (check_domain) domain error."""
+    check(load().fc2t2_plan_check(plan, stream))
 
 
 def profile_enable(plan: int, enable: bool) -> None:

@@ -281,17 +281,26 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     return FC2T2_OK;
 }
 
-static fc2t2_status finish_flags(fc2t2_plan_s *pl, cudaStream_t s) {
-    if (!pl->desc.check_domain) return FC2T2_OK;
-    int flags[2] = {0, 0};
-    fc2t2_status st = check_cuda(cudaMemcpyAsync(flags, pl->d_flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, s),
+// flags[0]: domain (cleared by every call); flags[2]: a tensor-core wait gave up (sticky until
+// fc2t2_plan_check)
+static fc2t2_status read_flags(fc2t2_plan_s *pl, cudaStream_t s, bool clear_sticky) {
+    int flags[3] = {0, 0, 0};
+    fc2t2_status st = check_cuda(cudaMemcpyAsync(flags, pl->d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s),
                                  "read flags");
     if (st != FC2T2_OK) return st;
+    if (clear_sticky &&
+        (st = check_cuda(cudaMemsetAsync(pl->d_flags + 2, 0, sizeof(int), s), "clear flags")) != FC2T2_OK)
+        return st;
     st = check_cuda(cudaStreamSynchronize(s), "synchronise");
     if (st != FC2T2_OK) return st;
-    if (flags[1]) return set_error(FC2T2_ERR_TIMEOUT, "a device-side wait of the tensor-core M2L gave up");
-    if (flags[0] & 1) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
+    if (flags[2]) return set_error(FC2T2_ERR_TIMEOUT, "a device-side wait of the tensor-core M2L gave up");
+    if (pl->desc.check_domain && (flags[0] & 1)) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
     return FC2T2_OK;
+}
+
+static fc2t2_status finish_flags(fc2t2_plan_s *pl, cudaStream_t s) {
+    if (!pl->desc.check_domain) return FC2T2_OK;
+    return read_flags(pl, s, false);
 }
 
 // ---------------------------------------------------------------- stage profiling
@@ -349,6 +358,10 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
     }
     // M2L of every level (independent given the moments): the tensor-core levels in one launch,
     // the others on the CUDA cores; then L2L from the coarsest level down
+    if (pl->tc.enabled) {
+        StageScope scope(pl, s, FC2T2_STAGE_M2L_PACK);
+        if ((st = check_cuda(launch_tc_pack(pl, s), "m2l operand pack")) != FC2T2_OK) return st;
+    }
     {
         StageScope scope(pl, s, FC2T2_STAGE_M2L);
         if (pl->tc.enabled && (st = check_cuda(launch_m2l_tc_all(pl, s), "m2l (tensor cores)")) != FC2T2_OK)
@@ -477,6 +490,11 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     return finish_flags(pl, s);
 }
 
+fc2t2_status fc2t2_plan_check(fc2t2_plan pl, void *stream) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    return read_flags(pl, static_cast<cudaStream_t>(stream), true);
+}
+
 fc2t2_status fc2t2_profile_enable(fc2t2_plan pl, int enable) {
     if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
     pl->profiling = enable != 0;
@@ -559,6 +577,7 @@ fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {
     bytes += (int64_t)pl->mma_ops_bytes + pl->tc.packed_bytes;
     bytes += (pl->src.cap + pl->qry.cap) * (int64_t)(5 * sizeof(int) + (pl->D + 1) * sizeof(float));
     info->device_bytes = bytes;
+    info->m2l_classes_per_cta = pl->tc.enabled ? pl->tc.ncls : 0;
     return FC2T2_OK;
 }
 

@@ -111,7 +111,11 @@ struct fc2t2_plan_s {
     void *d_mma_ops = nullptr;    // tensor-core M2L operator images (TF32 / BF16 modes)
     size_t mma_ops_bytes = 0;
     struct TcInfo {
-        int enabled = 0, mode = 0, img_bytes = 0, ncomp = 1, pn = 0, kbytes = 0, nchunks = 0;
+        int enabled = 0, mode = 0, img_bytes = 0, ncomp = 1, kbytes = 0, nchunks = 0;
+        int ncls = 1;      // target parity classes one CTA accumulates (sharing its moment views)
+        int ksc = 0;       // K-step capacity class of the kernel variant
+        int kh = 0;        // coefficients per epilogue column half
+        int pnb = 0;       // accumulator columns per TMEM buffer (2 * ncls * kh)
         int n0[24] = {}, N[24] = {}, K[24] = {}, b_off[24] = {};
         int nbuf = 1, nbslots = 2, smem = 0, tmem_cols = 32;
         double mma_flops = 0.0;                       // tensor-core work issued per transform
@@ -123,12 +127,12 @@ struct fc2t2_plan_s {
     } tc;
 
     // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage
-    mutable int64_t launches[FC2T2_NUM_STAGES] = {0, 0, 0, 0, 0, 0};
+    mutable int64_t launches[FC2T2_NUM_STAGES] = {};
     bool profiling = false;
     struct EventPair { int stage; cudaEvent_t a, b; };
     std::vector<EventPair> pending;
     std::vector<cudaEvent_t> event_pool;
-    double stage_ms[FC2T2_NUM_STAGES] = {0, 0, 0, 0, 0, 0};
+    double stage_ms[FC2T2_NUM_STAGES] = {};
 };
 
 namespace fc2t2 {
@@ -149,6 +153,7 @@ cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w);
+cudaError_t launch_tc_pack(const fc2t2_plan_s *pl, cudaStream_t s);
 cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s);
 // register-resident M2M / L2L for orders <= 6 (return false when not applicable)
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);

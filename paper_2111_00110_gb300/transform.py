@@ -84,6 +84,12 @@ class Plan:
         """Per-transform work of this plan (levels, P, M2L cell pairs and flops, device bytes)."""
         return capi.plan_query(self._h)
 
+    def check(self) -> None:
+        """Wait for the plan's work on the current stream and raise FC2T2Error if a bounded
+        device-side wait gave up since the last check (or, with check_domain, a point was outside
+        the domain in the last call)."""
+        capi.plan_check(self._h, self._stream())
+
     def _stream(self) -> int:
         return torch.cuda.current_stream(self.device).cuda_stream
 
@@ -137,3 +143,42 @@ class FC2T2Function(torch.autograd.Function):
 def fc2t2(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable explicit layer y = f(q; p, w) (Sec. 4)."""
     return FC2T2Function.apply(p, w, q, plan)
+
+
+def forward_batched(plans: Sequence[Plan], ps, ws, qs):
+    """Forward transforms of independent instances (one plan each, uneven N_i and M_i) through
+    one ``fc2t2_forward_batched`` call on the current stream; returns the list of y_i."""
+    n = len(plans)
+    if not (len(ps) == len(ws) == len(qs) == n):
+        raise ValueError("plans, ps, ws and qs must have the same length")
+    ys = []
+    for i, (pl, p, w, q) in enumerate(zip(plans, ps, ws, qs)):
+        _check_tensor(p, f"p[{i}]", (p.shape[0], pl.dim))
+        _check_tensor(w, f"w[{i}]", (p.shape[0],))
+        _check_tensor(q, f"q[{i}]", (q.shape[0], pl.dim))
+        ys.append(torch.empty(q.shape[0], device=q.device, dtype=torch.float32))
+    stream = torch.cuda.current_stream(plans[0].device).cuda_stream if n else 0
+    capi.forward_batched([pl._h for pl in plans], stream, [_ptr(p) for p in ps], [_ptr(w) for w in ws],
+                         [p.shape[0] for p in ps], [_ptr(q) for q in qs], [q.shape[0] for q in qs],
+                         [_ptr(y) for y in ys])
+    return ys
+
+
+def backward_batched(plans: Sequence[Plan], ps, ws, qs, ybars):
+    """(wbar_i, pbar_i) of independent instances through one ``fc2t2_backward_batched`` call."""
+    n = len(plans)
+    if not (len(ps) == len(ws) == len(qs) == len(ybars) == n):
+        raise ValueError("plans, ps, ws, qs and ybars must have the same length")
+    wbars, pbars = [], []
+    for i, (pl, p, w, q, yb) in enumerate(zip(plans, ps, ws, qs, ybars)):
+        _check_tensor(p, f"p[{i}]", (p.shape[0], pl.dim))
+        _check_tensor(w, f"w[{i}]", (p.shape[0],))
+        _check_tensor(q, f"q[{i}]", (q.shape[0], pl.dim))
+        _check_tensor(yb, f"ybar[{i}]", (q.shape[0],))
+        wbars.append(torch.empty(p.shape[0], device=p.device, dtype=torch.float32))
+        pbars.append(torch.empty(p.shape[0], pl.dim, device=p.device, dtype=torch.float32))
+    stream = torch.cuda.current_stream(plans[0].device).cuda_stream if n else 0
+    capi.backward_batched([pl._h for pl in plans], stream, [_ptr(p) for p in ps], [_ptr(w) for w in ws],
+                          [p.shape[0] for p in ps], [_ptr(q) for q in qs], [q.shape[0] for q in qs],
+                          [_ptr(y) for y in ybars], [_ptr(t) for t in wbars], [_ptr(t) for t in pbars])
+    return list(zip(wbars, pbars))

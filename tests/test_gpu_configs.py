@@ -1,0 +1,196 @@
+"""GPU parity of the other workload shapes: the ray-query workload at full size (sampled against
+the oracle), the batched uneven instances through the batched entry points, CUDA-graph replay of
+a plan, and a small fitting loop through the autograd layer.
+
+Bars: the FP32-accurate forms (plain FP32, TF32 x 3, BF16 x 3) within 1e-5 relative L2 of the
+oracle; single-pass TF32 within 1e-3 (the mixed-precision bar); single-pass BF16 within 1e-2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2111_00110_gb300 import workloads
+from test_gpu_parity import assert_close, f64, lib, make_plan, odesc, rel_l2  # noqa: F401
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+BARS = {"fp32": (1e-5, 1e-4), "tf32x3": (1e-5, 1e-4), "bf16x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2),
+        "bf16": (1e-2, 5e-2)}
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+# ------------------------------------------------------------------ ray queries, full size
+
+@pytest.fixture(scope="module")
+def rays():
+    """2^18 sphere-surface sources, 512 x 512 pinhole rays x 128 stratified samples (33.5M
+    queries), sigma 0.01, 64^3, order 8; the oracle at 4096 seeded queries (forward) and 4096
+    seeded sources (backward, cotangent seeded N(0,1) over all queries)."""
+    wl = workloads.sphere_rays()
+    rng = np.random.default_rng(33)
+    sq = np.sort(rng.choice(wl.M, size=4096, replace=False))
+    sp = np.sort(rng.choice(wl.N, size=4096, replace=False))
+    ybar = np.random.default_rng(34).standard_normal(wl.M).astype(np.float32)
+    d = odesc(3, wl.grid, wl.order, wl.sigma)
+    yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q), sel=sq)
+    wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, ybar), sel=sp)
+    return wl, sq, sp, ybar, yo, wo, po
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3", "tf32", "bf16"])
+def test_sphere_rays_full_size(lib, rays, mode):
+    wl, sq, sp, ybar, yo, wo, po = rays
+    plan = make_plan(3, wl.grid, wl.order, wl.sigma, wl.N, wl.M, m2l=mode)
+    p, w, q = dev(wl.p), dev(wl.w), dev(wl.q)
+    y = plan.forward(p, w, q)
+    wbar, pbar = plan.backward(p, w, q, dev(ybar))
+    torch.cuda.synchronize()
+    plan.check()
+    rel, elem = BARS[mode]
+    got_y = y.cpu().numpy()[sq]
+    print(f"sphere_rays {mode}: y {rel_l2(got_y, yo):.2e} wbar {rel_l2(wbar.cpu().numpy()[sp], wo):.2e} "
+          f"pbar {rel_l2(pbar.cpu().numpy()[sp], po):.2e}")
+    assert_close(got_y, yo, rel=rel, elem=elem, what=f"sphere_rays y ({mode})")
+    assert_close(wbar.cpu().numpy()[sp], wo, rel=rel, elem=elem, what=f"sphere_rays wbar ({mode})")
+    assert_close(pbar.cpu().numpy()[sp], po, rel=rel, elem=elem, what=f"sphere_rays pbar ({mode})")
+    plan.close()
+
+
+# ------------------------------------------------------------------ batched uneven instances
+
+MIX = [(0, 32, 4), (1, 64, 6), (2, 32, 8), (3, 64, 4), (4, 32, 6)]
+
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3"])
+def test_mixture_batched_forward_backward(lib, mode):
+    """Five instances of the clustered workload (uneven N_i = M_i, grids 32/64, orders 4-8) in one
+    batched forward and one batched backward call; each checked against the oracle at 2048 sampled
+    outputs."""
+    from paper_2111_00110_gb300.transform import backward_batched, forward_batched
+    wls = [workloads.mixture(i, grid=g, order=o) for i, g, o in MIX]
+    plans = [make_plan(3, wl.grid, wl.order, wl.sigma, wl.N, wl.M, m2l=mode) for wl in wls]
+    ps, ws, qs = [dev(wl.p) for wl in wls], [dev(wl.w) for wl in wls], [dev(wl.q) for wl in wls]
+    ybars = [dev(wl.ybar()) for wl in wls]
+    ys = forward_batched(plans, ps, ws, qs)
+    grads = backward_batched(plans, ps, ws, qs, ybars)
+    torch.cuda.synchronize()
+    for pl in plans:
+        pl.check()
+    rel, elem = BARS[mode]
+    for wl, y, (wbar, pbar), yb in zip(wls, ys, grads, ybars):
+        rng = np.random.default_rng(wl.seed)
+        sq = np.sort(rng.choice(wl.M, size=min(2048, wl.M), replace=False))
+        sp = np.sort(rng.choice(wl.N, size=min(2048, wl.N), replace=False))
+        d = odesc(3, wl.grid, wl.order, wl.sigma)
+        yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q), sel=sq)
+        wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, yb.cpu().numpy()), sel=sp)
+        tag = f"{wl.name} n{wl.grid} rho{wl.order} N{wl.N} ({mode})"
+        assert_close(y.cpu().numpy()[sq], yo, rel=rel, elem=elem, what=f"{tag} y")
+        assert_close(wbar.cpu().numpy()[sp], wo, rel=rel, elem=elem, what=f"{tag} wbar")
+        assert_close(pbar.cpu().numpy()[sp], po, rel=rel, elem=elem, what=f"{tag} pbar")
+    for pl in plans:
+        pl.close()
+
+
+def test_batched_empty_and_single(lib):
+    """An empty batch is a no-op; a batch of one equals the unbatched call."""
+    from paper_2111_00110_gb300.transform import forward_batched
+    assert forward_batched([], [], [], []) == []
+    wl = workloads.mixture(5, grid=32, order=4, n_override=3000)
+    plan = make_plan(3, wl.grid, wl.order, wl.sigma, wl.N, wl.M)
+    p, w, q = dev(wl.p), dev(wl.w), dev(wl.q)
+    (yb,) = forward_batched([plan], [p], [w], [q])
+    y = plan.forward(p, w, q)
+    torch.cuda.synchronize()
+    assert rel_l2(yb.cpu().numpy(), y.cpu().numpy()) <= 1e-6
+
+
+# ------------------------------------------------------------------ CUDA graph replay
+
+@pytest.mark.parametrize("mode", ["fp32", "bf16x3"])
+def test_cuda_graph_replay(lib, mode):
+    """Forward + backward of a plan captured once in a CUDA graph and replayed on new inputs
+    written into the captured buffers: the replay equals eager calls on the same inputs (to the
+    rounding of the within-cell summation order, which the counting sort does not fix)."""
+    grid, order, N, M = 32, 6, 20000, 15000
+    plan = make_plan(3, grid, order, 0.04, N, M, m2l=mode)
+    wl0 = workloads.uniform(41, 3, N, M, grid, order, 0.04)
+    p, w, q = dev(wl0.p), dev(wl0.w), dev(wl0.q)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                      # warm up outside capture
+        y = plan.forward(p, w, q)
+        plan.backward(p, w, q, y)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        y = plan.forward(p, w, q)
+        wbar, pbar = plan.backward(p, w, q, y)
+    for seed in (42, 43):
+        wl = workloads.uniform(seed, 3, N, M, grid, order, 0.04)
+        p.copy_(dev(wl.p)); w.copy_(dev(wl.w)); q.copy_(dev(wl.q))
+        g.replay()
+        torch.cuda.synchronize()
+        yg, wg, pg = y.cpu().numpy(), wbar.cpu().numpy(), pbar.cpu().numpy()
+        ye = plan.forward(p, w, q)
+        we, pe = plan.backward(p, w, q, ye)
+        torch.cuda.synchronize()
+        assert rel_l2(yg, ye.cpu().numpy()) <= 1e-6
+        assert rel_l2(wg, we.cpu().numpy()) <= 1e-6
+        assert rel_l2(pg, pe.cpu().numpy()) <= 1e-6
+    del g
+    plan.close()
+
+
+# ------------------------------------------------------------------ fitting loop (small)
+
+def test_fit_loop_small(lib):
+    """The fitting workload's shape at 2^17 sources and queries (128^3, order 8, sigma 0.005, TF32
+    M2L): targets from a ground-truth source set; Adam on (w, p) through the autograd layer.
+    Step 0's loss and gradients are checked against the oracle on samples; the loss falls."""
+    from paper_2111_00110_gb300.transform import fc2t2
+    n = 1 << 17
+    gt = workloads.fit_large(N=n, M=n)
+    plan = make_plan(3, gt.grid, gt.order, gt.sigma, n, n, m2l="tf32")
+    q = dev(gt.q)
+    with torch.no_grad():
+        target = plan.forward(dev(gt.p), dev(gt.w), q)
+    w0 = 0.1 * np.random.default_rng(5002).standard_normal(n).astype(np.float32)
+    p = dev(gt.p).requires_grad_(True)
+    w = dev(w0).requires_grad_(True)
+    # step 0 against the oracle
+    y = fc2t2(p, w, q, plan)
+    loss = torch.mean((y - target) ** 2)
+    loss.backward()
+    torch.cuda.synchronize()
+    d = odesc(3, gt.grid, gt.order, gt.sigma)
+    rng = np.random.default_rng(7)
+    sq = np.sort(rng.choice(n, size=2048, replace=False))
+    sp = np.sort(rng.choice(n, size=2048, replace=False))
+    yo = oracle.forward(d, *f64(gt.p, w0, gt.q), sel=sq)
+    assert rel_l2(y.detach().cpu().numpy()[sq], yo) <= 1e-3
+    ybar = (2.0 / n) * (y - target).detach().cpu().numpy()
+    wo, po = oracle.backward(d, *f64(gt.p, w0, gt.q, ybar), sel=sp)
+    assert rel_l2(w.grad.cpu().numpy()[sp], wo) <= 1e-3
+    assert rel_l2(p.grad.cpu().numpy()[sp], po) <= 1e-3
+    # a few Adam steps (lr 1e-3)
+    opt = torch.optim.Adam([w, p], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    losses = [float(loss)]
+    for _ in range(10):
+        opt.zero_grad()
+        with torch.no_grad():
+            p.clamp_(0.0, float(np.nextafter(np.float32(1.0), np.float32(0.0))))
+        loss = torch.mean((fc2t2(p, w, q, plan) - target) ** 2)
+        loss.backward()
+        opt.step()
+        losses.append(float(loss))
+    plan.check()
+    assert all(np.isfinite(losses))
+    assert losses[-1] < losses[0] and losses[1] < losses[0], losses
+    plan.close()

@@ -55,6 +55,7 @@ def run_forward(plan, p, w, q):
     P_, W_, Q_ = to_dev(p, w, q)
     y = plan.forward(P_, W_, Q_)
     torch.cuda.synchronize()
+    plan.check()
     return y.cpu().numpy()
 
 
@@ -62,6 +63,7 @@ def run_backward(plan, p, w, q, ybar):
     P_, W_, Q_, YB = to_dev(p, w, q, ybar)
     wbar, pbar = plan.backward(P_, W_, Q_, YB)
     torch.cuda.synchronize()
+    plan.check()
     return wbar.cpu().numpy(), pbar.cpu().numpy()
 
 
@@ -253,11 +255,26 @@ def test_uniform3d_full_size_forward_backward(lib):
 TC_BARS = {"tf32x3": (1e-5, 1e-4), "bf16x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2), "bf16": (1e-2, 5e-2)}
 
 
+# Target parity classes one tensor-core CTA accumulates, by (mode, order); 0 = the M2L stays on the
+# CUDA cores (the operands do not fit shared memory).  Orders <= 5 share each moment view among
+# four classes, 6 (and 7 for BF16) among two.
+TC_CLASSES = {
+    "bf16": {1: 4, 2: 4, 3: 4, 4: 4, 5: 4, 6: 2, 7: 2, 8: 1},
+    "bf16x3": {1: 4, 2: 4, 3: 4, 4: 4, 5: 4, 6: 2, 7: 1, 8: 1},
+    "tf32": {1: 4, 2: 4, 3: 4, 4: 4, 5: 4, 6: 2, 7: 1, 8: 1},
+    "tf32x3": {1: 4, 2: 4, 3: 4, 4: 4, 5: 2, 6: 1, 7: 0, 8: 0},
+}
+
+
 @pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32", "bf16"])
-@pytest.mark.parametrize("grid,order", [(16, 4), (16, 6), (32, 6), (8, 3)])
+@pytest.mark.parametrize("grid,order", [(16, 4), (16, 6), (32, 6), (8, 3), (8, 1), (16, 2), (16, 5), (16, 7),
+                                        (16, 8)])
 def test_tensor_core_m2l_forward(lib, mode, grid, order):
     wl = workloads.uniform(500 + grid + order, 3, 6000, 5000, grid, order, 1.3 / grid)
     plan = make_plan(3, grid, order, wl.sigma, wl.N, wl.M, m2l=mode)
+    info = plan.info()
+    assert info["m2l_classes_per_cta"] == TC_CLASSES[mode][order]
+    assert info["m2l_tensor_cores"] == (1 if TC_CLASSES[mode][order] else 0)
     y = run_forward(plan, wl.p, wl.w, wl.q)
     yo = oracle.forward(odesc(3, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
     rel, elem = TC_BARS[mode]
