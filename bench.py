@@ -39,6 +39,9 @@ METRIC = "fwd+bwd query-evals/s"
 UNIT = "query-evals/s"
 # nominal dense tensor-core ratios (TF32 : BF16 = 1.1 : 2.25 PFLOP/s per GPU)
 TF32_PER_BF16 = 1.1 / 2.25
+# DRAM bytes (read + write) of one M2L launch, from an ncu capture of the current kernel build
+# (profiles/k_m2l_tc_bf16x3_uniform3d.md); None where no capture of the current build exists
+M2L_TRAFFIC_BYTES = {"bf16x3": 442.120960e6 + 82.223104e6}
 
 
 def parse():
@@ -47,7 +50,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--m2l", default="auto", choices=["auto", "tf32x3", "bf16x3", "tf32", "bf16", "fp32"])
+    ap.add_argument("--m2l", default="auto", choices=["auto", "separable", "tf32x3", "bf16x3", "tf32", "bf16", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
@@ -336,9 +339,37 @@ def roofline_for(m: Measured, peaks):
         basis += " x nominal TF32/BF16 ratio 1.1/2.25"
     executed = issued / (m2l_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": None, "kernel": f"k_m2l_tc (tcgen05, {m.mode})", "flops_per_step": useful,
+            "traffic": M2L_TRAFFIC_BYTES.get(m.mode), "traffic_unit": "bytes per launch (one transform)",
+            "kernel": f"k_m2l_tc (tcgen05, {m.mode})", "flops_per_step": useful,
             "executed": {"flops_per_step": issued, "achieved": executed, "frac": executed / peak},
             "peak_basis": basis}
+
+
+def stage_roofline(m: Measured, wl, peaks):
+    """HBM roofline of the memory-bound stages, per step (forward + backward): the bytes each
+    stage must move (inputs read once, outputs written once) over its measured time."""
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    P = m.info["coefficients"]
+    Pp = (P + 3) // 4 * 4
+    row = 4 * Pp
+    G = [(wl.grid >> l) ** 3 for l in range(m.info["levels"])]
+    N, M = wl.N, wl.M
+    # per transform; the forward has sources (p, w) and targets q, the backward sources (q, ybar)
+    # and targets p (with w for pbar)
+    sort = (12 + 4 + 16 + 4) * N + (12 + 12 + 4) * M          # fwd: sort p,w; sort q
+    sort += (12 + 4 + 16 + 4) * M + (12 + 4 + 16 + 4) * N      # bwd: sort q,ybar; sort p,w
+    p2m = (16 * N + row * G[0]) + (16 * M + row * G[0])
+    m2m = 2 * sum(row * (G[l] + G[l + 1]) for l in range(len(G) - 1))
+    l2l = 2 * sum(row * (G[l + 1] + 2 * G[l]) for l in range(len(G) - 1))
+    l2p = (12 * M + row * G[0] + 4 * M) + (16 * N + row * G[0] + 16 * N)
+    out = {}
+    for name, b in (("sort", sort), ("p2m", p2m), ("m2m", m2m), ("l2l", l2l), ("l2p", l2p)):
+        ms = m.stage_ms.get(name)
+        if not ms:
+            continue
+        gbs = b / (ms / 1e3) / 1e9
+        out[name] = {"bytes_per_step": b, "achieved_gbs": gbs, "frac_of_hbm": gbs / hbm}
+    return out
 
 
 def run_ours(args, rank, world, local_rank):
@@ -397,6 +428,8 @@ def run_ours(args, rank, world, local_rank):
         "e2e": main.e2e,
         "gpu_launches": main.launches,
         "roofline": roofline_for(main, peaks),
+        "stage_roofline": {"peak_gbs": peaks.get("hbm_gbs"), "peak_basis": "of measured hbm copy (MEASURED_PEAKS.json)",
+                           "stages": stage_roofline(main, wl, peaks)},
         "stage_ms_per_step": main.stage_ms,
         "variants": {k: summary(v) for k, v in variants.items()},
         "cpu_baseline": cpu,

@@ -70,15 +70,19 @@ typedef enum {
 } fc2t2_kernel;
 
 /* Arithmetic of the M2L translation, the dominant step.  The tensor-core forms apply to 3D
- * plans; 2D plans run the CUDA-core M2L whatever is asked. */
+ * plans; 2D plans run the CUDA-core M2L whatever is asked.  SEPARABLE needs the Gaussian kernel
+ * and dim = 3 (plan creation returns UNSUPPORTED otherwise). */
 typedef enum {
     FC2T2_M2L_FP32 = 0,          /* FP32 on the CUDA cores */
     FC2T2_M2L_TF32 = 1,          /* tcgen05 tensor cores, TF32 operands, FP32 accumulation */
     FC2T2_M2L_BF16 = 2,          /* tcgen05 tensor cores, BF16 operands, FP32 accumulation */
     FC2T2_M2L_TF32X3 = 3,        /* tcgen05, each operand split into TF32 high + low parts,
                                     three products (hi*hi + hi*lo + lo*hi): FP32 accuracy */
-    FC2T2_M2L_BF16X3 = 4         /* as TF32X3 with BF16 parts (~16 significant bits per operand,
+    FC2T2_M2L_BF16X3 = 4,        /* as TF32X3 with BF16 parts (~16 significant bits per operand,
                                     half the MMA instructions): within the FP32 error bar */
+    FC2T2_M2L_SEPARABLE = 5      /* FP32 on the CUDA cores, the Gaussian's derivative table
+                                    factored per dimension: three one-dimensional passes per
+                                    level (same operator and interaction lists, far fewer flops) */
 } fc2t2_m2l_prec;
 
 typedef struct fc2t2_plan_s *fc2t2_plan;

@@ -24,7 +24,7 @@ STATUS = {
     6: "FC2T2_ERR_TIMEOUT",
 }
 KERNELS = {"gaussian": 0, "poly": 1}
-M2L_PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
+M2L_PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4, "separable": 5}
 
 # every entry point declared in include/fc2t2.h
 EXPORTS = (

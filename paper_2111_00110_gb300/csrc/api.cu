@@ -123,7 +123,7 @@ static fc2t2_status upload(T *dst, const std::vector<T> &src, const char *what) 
 
 static void free_sort(SortWork &w) {
     cudaFree(w.count); cudaFree(w.start); cudaFree(w.key); cudaFree(w.rank);
-    cudaFree(w.perm); cudaFree(w.key_sorted); cudaFree(w.pts); cudaFree(w.wts);
+    cudaFree(w.perm); cudaFree(w.rec);
     w = SortWork();
 }
 
@@ -135,9 +135,7 @@ static fc2t2_status alloc_sort(SortWork &w, int64_t cap, int64_t G0, int D) {
     if ((st = dev_alloc(&w.key, cap, "keys")) != FC2T2_OK) return st;
     if ((st = dev_alloc(&w.rank, cap, "ranks")) != FC2T2_OK) return st;
     if ((st = dev_alloc(&w.perm, cap, "permutation")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&w.key_sorted, cap, "sorted keys")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&w.pts, cap * D, "sorted points")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&w.wts, cap, "sorted weights")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&w.rec, cap, "sorted points")) != FC2T2_OK) return st;
     return FC2T2_OK;
 }
 
@@ -151,6 +149,7 @@ static void destroy(fc2t2_plan_s *pl) {
     cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
     cudaFree(pl->d_mma_ops);
     for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
+    cudaFree(pl->sep.d_t);
     free_sort(pl->src);
     free_sort(pl->qry);
     delete pl;
@@ -241,6 +240,7 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
     if ((st = upload(pl->d_m2l_start, m2l_start, "upload m2l index")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_m2l_pairs, m2l_pairs, "upload m2l pairs")) != FC2T2_OK) return st;
     // tensor-core operator images (3D; other dimensions keep the CUDA-core M2L)
+    if (pl->desc.m2l == FC2T2_M2L_SEPARABLE) return build_sep(pl, dtab64);
     if (pl->desc.m2l != FC2T2_M2L_FP32 && D == 3)
         if ((st = build_tc_operators(pl, dtab64)) != FC2T2_OK) return st;
     return FC2T2_OK;
@@ -270,8 +270,10 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     }
     if (d->channels != 1) return set_error(FC2T2_ERR_UNSUPPORTED, "only channels == 1 is supported");
     if (d->m2l != FC2T2_M2L_FP32 && d->m2l != FC2T2_M2L_TF32 && d->m2l != FC2T2_M2L_BF16 &&
-        d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3)
+        d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3 && d->m2l != FC2T2_M2L_SEPARABLE)
         return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
+    if (d->m2l == FC2T2_M2L_SEPARABLE && (d->kernel != FC2T2_KERNEL_GAUSSIAN || d->dim != 3))
+        return set_error(FC2T2_ERR_UNSUPPORTED, "the separable M2L needs the Gaussian kernel and dim = 3");
     if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||
         d->max_queries > (int64_t)INT32_MAX)
         return set_error(FC2T2_ERR_INVALID_ARG, "max_sources / max_queries out of range");
@@ -364,11 +366,15 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
     }
     {
         StageScope scope(pl, s, FC2T2_STAGE_M2L);
-        if (pl->tc.enabled && (st = check_cuda(launch_m2l_tc_all(pl, s), "m2l (tensor cores)")) != FC2T2_OK)
-            return st;
-        for (int l = pl->nlev - 1; l >= 0; --l)
-            if (!(pl->tc.enabled && pl->tc.level_ok[l]))
-                if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
+        if (pl->sep.enabled) {
+            if ((st = check_cuda(launch_m2l_sep(pl, s), "m2l (separable)")) != FC2T2_OK) return st;
+        } else {
+            if (pl->tc.enabled && (st = check_cuda(launch_m2l_tc_all(pl, s), "m2l (tensor cores)")) != FC2T2_OK)
+                return st;
+            for (int l = pl->nlev - 1; l >= 0; --l)
+                if (!(pl->tc.enabled && pl->tc.level_ok[l]))
+                    if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
+        }
     }
     for (int l = pl->nlev - 2; l >= 0; --l) {
         StageScope scope(pl, s, FC2T2_STAGE_L2L);
@@ -567,14 +573,15 @@ fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {
         }
         const double pairs = std::pow(W, pl->D) - (l > 0 ? std::pow(H, pl->D) : 0.0);
         pairs_total += pairs;
+        if (pl->sep.enabled) continue;
         if (pl->tc.enabled && pl->tc.level_ok[l]) issued += pl->tc.mma_flops_level[l];
         else issued += 2.0 * q * pairs;
     }
     info->m2l_cell_pairs = pairs_total;
     info->m2l_useful_flops = 2.0 * q * pairs_total;
-    info->m2l_issued_flops = issued;
+    info->m2l_issued_flops = pl->sep.enabled ? pl->sep.flops : issued;
     int64_t bytes = 2 * pl->G_total * pl->Pp * (int64_t)sizeof(float);
-    bytes += (int64_t)pl->mma_ops_bytes + pl->tc.packed_bytes;
+    bytes += (int64_t)pl->mma_ops_bytes + pl->tc.packed_bytes + (int64_t)pl->sep.t_bytes;
     bytes += (pl->src.cap + pl->qry.cap) * (int64_t)(5 * sizeof(int) + (pl->D + 1) * sizeof(float));
     info->device_bytes = bytes;
     info->m2l_classes_per_cta = pl->tc.enabled ? pl->tc.ncls : 0;

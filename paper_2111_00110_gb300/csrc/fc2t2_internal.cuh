@@ -68,9 +68,7 @@ struct SortWork {
     int *key = nullptr;         // [cap]  cell of point i (input order)
     int *rank = nullptr;        // [cap]  position of point i within its cell
     int *perm = nullptr;        // [cap]  sorted position -> input index
-    int *key_sorted = nullptr;  // [cap]  cell of sorted point
-    float *pts = nullptr;       // [cap][D] sorted positions
-    float *wts = nullptr;       // [cap]  sorted weights
+    float4 *rec = nullptr;      // [cap]  sorted point: (x0, x1, x2 or 0, weight or 0)
 };
 
 struct Level {
@@ -126,6 +124,17 @@ struct fc2t2_plan_s {
         alignas(64) unsigned char maps[fc2t2::kMaxLevels][2][128] = {};   // TMA descriptors (hi, lo)
     } tc;
 
+    struct SepInfo {             // separable-kernel M2L (Gaussian, 3D)
+        int enabled = 0, q4p = 0;
+        std::vector<float> dt_host;   // [nlev][7][rho + 1] scaled 1D derivatives dt_o(j)
+        float *d_t = nullptr;     // intermediate 4-indexed rows
+        size_t t_bytes = 0;
+        int64_t t_off[fc2t2::kMaxLevels][2][2] = {};   // [level][buffer][chain], in floats
+        int seg[fc2t2::kMaxLevels] = {};
+        size_t smem = 0;
+        double flops = 0.0;
+    } sep;
+
     // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage
     mutable int64_t launches[FC2T2_NUM_STAGES] = {};
     bool profiling = false;
@@ -154,6 +163,8 @@ cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w);
 cudaError_t launch_tc_pack(const fc2t2_plan_s *pl, cudaStream_t s);
+fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
+cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s);
 cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s);
 // register-resident M2M / L2L for orders <= 6 (return false when not applicable)
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);

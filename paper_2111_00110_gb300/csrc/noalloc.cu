@@ -40,8 +40,7 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr size_t kSortBytes =
     align256(sizeof(int) * kNaMaxCells) + align256(sizeof(int) * (kNaMaxCells + 1)) +
-    4 * align256(sizeof(int) * kNaMaxPoints) + align256(sizeof(float) * kNaMaxPoints * 3) +
-    align256(sizeof(float) * kNaMaxPoints);
+    3 * align256(sizeof(int) * kNaMaxPoints) + align256(sizeof(float4) * kNaMaxPoints);
 constexpr size_t kScratchBytes =
     2 * align256(sizeof(float) * kNaMaxCellsAllLevels * kNaMaxPp) +                  // M, L
     align256(sizeof(float) * kNaMaxLevels * kNaOffsets * kNaMaxPp) +                 // dtab
@@ -205,9 +204,7 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
         sw->key = carve<int>(base, off, kNaMaxPoints);
         sw->rank = carve<int>(base, off, kNaMaxPoints);
         sw->perm = carve<int>(base, off, kNaMaxPoints);
-        sw->key_sorted = carve<int>(base, off, kNaMaxPoints);
-        sw->pts = carve<float>(base, off, kNaMaxPoints * 3);
-        sw->wts = carve<float>(base, off, kNaMaxPoints);
+        sw->rec = carve<float4>(base, off, kNaMaxPoints);
     }
     if (off > kScratchBytes) return set_error(FC2T2_ERR_UNSUPPORTED, "scratch layout exceeds the array");
 

@@ -30,8 +30,7 @@ __device__ __forceinline__ void power_ladder(float u, float (&pw)[RHO + 1]) {
 constexpr int kP2MThreads = 64;
 
 template <int D, int RHO>
-__global__ void __launch_bounds__(kP2MThreads) k_p2m(const float *__restrict__ xs,
-                                                     const float *__restrict__ ws,
+__global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ rec,
                                                      const int *__restrict__ start, int n,
                                                      int64_t G, float lo, float h, float inv_h,
                                                      float *__restrict__ M) {
@@ -53,10 +52,12 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float *__restrict__ x
         for (int d = 0; d < D; ++d) z[d] = lo + ((float)cc[d] + 0.5f) * h;
         const int j0 = start[c], j1 = start[c + 1];
         for (int j = j0; j < j1; ++j) {
+            const float4 r = __ldg(rec + j);
+            const float xj[3] = {r.x, r.y, r.z};
             float pw[3][RHO + 1];
 #pragma unroll
-            for (int d = 0; d < D; ++d) power_ladder<RHO>((xs[(int64_t)j * D + d] - z[d]) * inv_h, pw[d]);
-            const float wj = ws[j];
+            for (int d = 0; d < D; ++d) power_ladder<RHO>((xj[d] - z[d]) * inv_h, pw[d]);
+            const float wj = r.w;
 #pragma unroll
             for (int a0 = 0; a0 <= RHO; ++a0) {
                 const float t0 = wj * pw[0][a0];
@@ -94,7 +95,7 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     cudaError_t err = cudaSuccess;
     pl->launches[FC2T2_STAGE_P2M] += 1;
     FC2T2_DISPATCH(pl->D, pl->rho,
-                   (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.pts, w.wts, w.start, pl->n, G,
+                   (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.rec, w.start, pl->n, G,
                                                                     pl->lo_f, h, inv_h, M0),
                     err = cudaGetLastError()),
                    return cudaErrorInvalidValue)
@@ -104,26 +105,29 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
 constexpr int kL2PThreads = 128;
 
 template <int D, int RHO, bool GRAD>
-__global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float *__restrict__ xs,
-                                                     const int *__restrict__ key_sorted,
+__global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float4 *__restrict__ rec,
                                                      const int *__restrict__ perm,
-                                                     const float *__restrict__ ws,
-                                                     const float *__restrict__ L, int n, float lo,
+                                                     const float *__restrict__ L, int n, float lo, float scale,
                                                      float h, float inv_h, float *__restrict__ val,
                                                      float *__restrict__ grad) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     const int64_t j = (int64_t)blockIdx.x * kL2PThreads + threadIdx.x;
     if (j >= m) return;
-    const int c = key_sorted[j];
+    const float4 r = __ldg(rec + j);
+    const float xj[3] = {r.x, r.y, r.z};
     float pw[3][RHO + 1];
+    int c = 0;
     {
-        int r = c;
+        // the point's cell by the binning rule of the sort (same FP32 steps, same result)
+        int cd[3];
+#pragma unroll
+        for (int d = 0; d < D; ++d) cd[d] = cell_of(xj[d], lo, scale, n);
+#pragma unroll
+        for (int d = D - 1; d >= 0; --d) c = c * n + cd[d];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-            const int cd = r % n;
-            r /= n;
-            const float z = lo + ((float)cd + 0.5f) * h;
-            power_ladder<RHO>((xs[j * D + d] - z) * inv_h, pw[d]);
+            const float z = lo + ((float)cd[d] + 0.5f) * h;
+            power_ladder<RHO>((xj[d] - z) * inv_h, pw[d]);
         }
     }
     float Lv[Pp];
@@ -168,7 +172,7 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float *__r
     const int i = perm[j];
     if (val) val[i] = value;
     if (GRAD && grad) {
-        const float s = ws[j] * inv_h;
+        const float s = r.w * inv_h;
         grad[(int64_t)i * D] = s * g0;
         grad[(int64_t)i * D + 1] = s * g1;
         if (D == 3) grad[(int64_t)i * D + 2] = s * g2;
@@ -186,15 +190,13 @@ cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     if (grad_times_w) {
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p<D_, R_, true><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.pts, w.key_sorted, w.perm, w.wts, L0, pl->n, pl->lo_f, h, inv_h, val,
-                            grad_times_w),
+                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, grad_times_w),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     } else {
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p<D_, R_, false><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.pts, w.key_sorted, w.perm, w.wts, L0, pl->n, pl->lo_f, h, inv_h, val,
-                            nullptr),
+                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, nullptr),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     }

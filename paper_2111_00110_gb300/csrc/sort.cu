@@ -6,9 +6,10 @@
 //   count   : cell of every point (FP32 rule), count[cell]++ (the returned old value is the
 //             point's rank inside its cell)
 //   scan    : exclusive prefix sum of the counts -> start[cell]        (reduce-then-scan)
-//   scatter : sorted position = start[cell] + rank; writes the permutation, the sorted
-//             cell keys and the sorted coordinates / weights (so P2M and L2P read
-//             contiguous, cell-ordered data).
+//   scatter : sorted position = start[cell] + rank; writes the permutation and one 16-byte
+//             record per point (coordinates and weight), so P2M and L2P read contiguous,
+//             cell-ordered data; a consumer that needs a point's cell recomputes it from the
+//             record with the same FP32 rule.
 // The order of points inside one cell depends on the order in which the atomics resolved;
 // every consumer only sums or evaluates per point, so results differ at most by rounding.
 #include "fc2t2_internal.cuh"
@@ -155,17 +156,12 @@ __global__ void __launch_bounds__(256) k_scatter(int64_t n, const int *__restric
                                                  const int *__restrict__ start,
                                                  const float *__restrict__ x,
                                                  const float *__restrict__ wt, int *__restrict__ perm,
-                                                 int *__restrict__ key_sorted, float *__restrict__ xs,
-                                                 float *__restrict__ ws) {
+                                                 float4 *__restrict__ rec) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    int k = key[i];
-    int64_t pos = (int64_t)start[k] + rank[i];
+    const int64_t pos = (int64_t)start[key[i]] + rank[i];
     perm[pos] = (int)i;
-    key_sorted[pos] = k;
-#pragma unroll
-    for (int d = 0; d < D; ++d) xs[pos * D + d] = x[i * D + d];
-    if (wt) ws[pos] = wt[i];
+    rec[pos] = make_float4(x[i * D], x[i * D + 1], D == 3 ? x[i * D + 2] : 0.0f, wt ? wt[i] : 0.0f);
 }
 
 cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt,
@@ -174,11 +170,9 @@ cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *
     unsigned blocks = (unsigned)((n + 255) / 256);
     pl->launches[FC2T2_STAGE_SORT] += 1;
     if (pl->D == 2)
-        k_scatter<2><<<blocks, 256, 0, s>>>(n, w.key, w.rank, w.start, x, wt, w.perm, w.key_sorted,
-                                            w.pts, w.wts);
+        k_scatter<2><<<blocks, 256, 0, s>>>(n, w.key, w.rank, w.start, x, wt, w.perm, w.rec);
     else
-        k_scatter<3><<<blocks, 256, 0, s>>>(n, w.key, w.rank, w.start, x, wt, w.perm, w.key_sorted,
-                                            w.pts, w.wts);
+        k_scatter<3><<<blocks, 256, 0, s>>>(n, w.key, w.rank, w.start, x, wt, w.perm, w.rec);
     return cudaGetLastError();
 }
 

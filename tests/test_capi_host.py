@@ -75,6 +75,16 @@ def test_polynomial_descriptor_needs_a_full_graded_block(lib):
     assert lib.fc2t2_plan_create(ctypes.byref(d), ctypes.byref(out)) == 1
 
 
+def test_separable_m2l_needs_the_gaussian_in_3d(lib):
+    out = ctypes.c_void_p(123)
+    assert lib.fc2t2_plan_create(ctypes.byref(_desc(m2l=5, dim=2)), ctypes.byref(out)) == 2
+    coef = (ctypes.c_double * 4)(*([1.0] * 4))   # degree-1 polynomial in 3D: C(4, 3) = 4
+    d = _desc(kernel=1, n_poly=4, m2l=5)
+    d.poly_coef = ctypes.cast(coef, ctypes.POINTER(ctypes.c_double))
+    assert lib.fc2t2_plan_create(ctypes.byref(d), ctypes.byref(out)) == 2
+    assert out.value is None
+
+
 def test_null_arguments(lib):
     assert lib.fc2t2_plan_create(None, None) == 1
     assert lib.fc2t2_forward(None, None, None, None, 0, None, 0, None) == 1

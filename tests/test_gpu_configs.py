@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-BARS = {"fp32": (1e-5, 1e-4), "tf32x3": (1e-5, 1e-4), "bf16x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2),
+BARS = {"fp32": (1e-5, 1e-4), "separable": (1e-5, 1e-4), "tf32x3": (1e-5, 1e-4), "bf16x3": (1e-5, 1e-4), "tf32": (1e-3, 1e-2),
         "bf16": (1e-2, 5e-2)}
 
 
@@ -42,7 +42,7 @@ def rays():
     return wl, sq, sp, ybar, yo, wo, po
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("mode", ["separable", "fp32", "bf16x3", "tf32", "bf16"])
 def test_sphere_rays_full_size(lib, rays, mode):
     wl, sq, sp, ybar, yo, wo, po = rays
     plan = make_plan(3, wl.grid, wl.order, wl.sigma, wl.N, wl.M, m2l=mode)
@@ -66,7 +66,7 @@ def test_sphere_rays_full_size(lib, rays, mode):
 MIX = [(0, 32, 4), (1, 64, 6), (2, 32, 8), (3, 64, 4), (4, 32, 6)]
 
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("mode", ["separable", "bf16x3"])
 def test_mixture_batched_forward_backward(lib, mode):
     """Five instances of the clustered workload (uneven N_i = M_i, grids 32/64, orders 4-8) in one
     batched forward and one batched backward call; each checked against the oracle at 2048 sampled
@@ -112,7 +112,7 @@ def test_batched_empty_and_single(lib):
 
 # ------------------------------------------------------------------ CUDA graph replay
 
-@pytest.mark.parametrize("mode", ["fp32", "bf16x3"])
+@pytest.mark.parametrize("mode", ["separable", "bf16x3"])
 def test_cuda_graph_replay(lib, mode):
     """Forward + backward of a plan captured once in a CUDA graph and replayed on new inputs
     written into the captured buffers: the replay equals eager calls on the same inputs (to the
@@ -192,5 +192,7 @@ def test_fit_loop_small(lib):
         losses.append(float(loss))
     plan.check()
     assert all(np.isfinite(losses))
-    assert losses[-1] < losses[0] and losses[1] < losses[0], losses
+    # losses[1] is taken before the first update; from there on every Adam step lowers the loss
+    assert losses[-1] < 0.8 * losses[0], losses
+    assert all(b <= a for a, b in zip(losses[1:], losses[2:])), losses
     plan.close()

@@ -282,6 +282,30 @@ def test_tensor_core_m2l_forward(lib, mode, grid, order):
     assert_close(y, yo, rel=rel, elem=elem, what=f"{mode} n{grid} rho{order}")
 
 
+# ----------------------------------------------------------------- separable M2L (3D Gaussian)
+
+@pytest.mark.parametrize("grid,order", [(16, 4), (16, 6), (32, 6), (8, 3), (8, 1), (16, 2), (16, 5), (16, 7),
+                                        (16, 8), (4, 4), (64, 4)])
+def test_separable_m2l_forward(lib, grid, order):
+    wl = workloads.uniform(900 + grid + order, 3, 6000, 5000, grid, order, 1.3 / grid)
+    plan = make_plan(3, grid, order, wl.sigma, wl.N, wl.M, m2l="separable")
+    assert plan.info()["m2l_tensor_cores"] == 0
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    yo = oracle.forward(odesc(3, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    print(f"separable n{grid} rho{order}: rel-L2 {rel_l2(y, yo):.3e}")
+    assert_close(y, yo, what=f"separable n{grid} rho{order}")
+
+
+def test_separable_m2l_backward(lib):
+    wl = workloads.uniform(778, 3, 4000, 3500, 16, 6, 0.08)
+    ybar = wl.ybar()
+    plan = make_plan(3, 16, 6, wl.sigma, wl.N, wl.M, m2l="separable")
+    wbar, pbar = run_backward(plan, wl.p, wl.w, wl.q, ybar)
+    wo, po = oracle.backward(odesc(3, 16, 6, wl.sigma), *f64(wl.p, wl.w, wl.q, ybar))
+    assert_close(wbar, wo, what="separable wbar")
+    assert_close(pbar, po, what="separable pbar")
+
+
 @pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32"])
 def test_tensor_core_m2l_backward(lib, mode):
     wl = workloads.uniform(777, 3, 4000, 3500, 16, 6, 0.08)
