@@ -9,11 +9,12 @@ oracle.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--m2l MODE]
 
-MODE "auto" (default) reports the FP32-accurate path (M2L on tcgen05 with BF16 x 3 split operands)
-as `value`, and as `variants` the other FP32-accurate split (TF32 x 3), the mixed-precision forms
-(single-pass TF32 and BF16 M2L) and the plain CUDA-core FP32 form, each with its measured error
-against the oracle on a seeded sample (4096 queries for y, 4096 sources for wbar and pbar with a
-fixed seeded cotangent).
+MODE "auto" (default) reports the fastest FP32-accurate path (the separable M2L: the Gaussian's
+factored derivatives in three 1D passes on the CUDA cores, FP32) as `value`, and as `variants` the
+tensor-core forms (BF16 x 3 and TF32 x 3 split operands, FP32-accurate; single-pass TF32 and BF16,
+mixed precision) and the plain CUDA-core FP32 form, each with its measured error against the
+oracle on a seeded sample (4096 queries for y, 4096 sources for wbar and pbar with a fixed seeded
+cotangent).
 
 Prints one JSON line on rank 0.  ``--impl reference`` times the FP64 CPU oracle on the host cores
 on a bounded sample of the same workload (the queries -- and, for the backward, the sources --
@@ -39,15 +40,17 @@ METRIC = "fwd+bwd query-evals/s"
 UNIT = "query-evals/s"
 # nominal dense tensor-core ratios (TF32 : BF16 = 1.1 : 2.25 PFLOP/s per GPU)
 TF32_PER_BF16 = 1.1 / 2.25
-# DRAM bytes (read + write) of one M2L launch, from an ncu capture of the current kernel build
-# (profiles/k_m2l_tc_bf16x3_uniform3d.md); None where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"bf16x3": 442.120960e6 + 82.223104e6}
+# DRAM bytes (read + write) of one transform's M2L launches, from an ncu capture of the current
+# kernel builds (profiles/k_m2l_sep_uniform3d.md, profiles/k_m2l_tc_bf16x3_uniform3d.md); None
+# where no capture of the current build exists
+M2L_TRAFFIC_BYTES = {"separable": (88.1 + 12.6 + 222.3 + 63.6 + 222.4 + 63.5 + 162.3 + 4.9 + 176.6 + 16.8 + 63.2 + 1.3) * 1e6,
+                     "bf16x3": (464.0 + 82.8) * 1e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--m2l", default="auto", choices=["auto", "separable", "tf32x3", "bf16x3", "tf32", "bf16", "fp32"])
@@ -95,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             threading.Thread(target=self._read, daemon=True).start()
         except Exception:
@@ -220,9 +223,11 @@ class Measured:
     pass
 
 
-def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, clocks=False):
-    """Time `args.steps` fwd+bwd steps of one M2L form; per-stage device times from the library's
-    events on the launching stream; optional end-to-end loop from pinned host buffers."""
+def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, clocks=False, steps=None):
+    """Time `steps` (default `args.steps`) fwd+bwd steps of one M2L form; per-stage device times
+    from the library's events on the launching stream; optional end-to-end loop from pinned host
+    buffers."""
+    nsteps = args.steps if steps is None else steps
     import torch
     from paper_2111_00110_gb300.transform import Plan
 
@@ -238,6 +243,7 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
 
     out = Measured()
     out.mode = mode
+    out.grid = wl.grid
     out.info = plan.info()
     # accuracy against the oracle sample (a seeded cotangent for the backward)
     if ref is not None:
@@ -260,10 +266,10 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
     sampler = ClockSampler(dev.index) if clocks else None
     if sampler:
         sampler.start()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
     torch.cuda.synchronize(dev)
-    for i in range(args.steps):
+    for i in range(nsteps):
         flush.zero_()                       # evict L2 between timed steps (not timed)
         starts[i].record(stream)
         step()
@@ -273,11 +279,11 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
     stage_ms, launches = plan.profile_read(reset=True)
     plan.profile(False)
     total_ms = aggregate_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
-    out.ms_per_step = total_ms / args.steps
-    out.value = wl.M * args.steps * world / (total_ms / 1e3)
-    out.stage_ms = {k: v / args.steps for k, v in stage_ms.items()}
+    out.ms_per_step = total_ms / nsteps
+    out.value = wl.M * nsteps * world / (total_ms / 1e3)
+    out.stage_ms = {k: v / nsteps for k, v in stage_ms.items()}
     out.launches = int(sum(launches.values()))
-    out.launches_per_step = {k: v / args.steps for k, v in launches.items()}
+    out.launches_per_step = {k: v / nsteps for k, v in launches.items()}
     out.e2e = None
     if do_e2e:
         hp, hw, hq = (torch.from_numpy(a).pin_memory() for a in (wl.p, wl.w, wl.q))
@@ -299,16 +305,32 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
         torch.cuda.synchronize(dev)
         es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         es.record(stream)
-        for _ in range(args.steps):
+        for _ in range(nsteps):
             e2e_step()
         ee.record(stream)
         torch.cuda.synchronize(dev)
         e2e_ms = aggregate_max(es.elapsed_time(ee), world, dev)
-        out.e2e = {"value": wl.M * args.steps * world / (e2e_ms / 1e3), "unit": UNIT,
+        out.e2e = {"value": wl.M * nsteps * world / (e2e_ms / 1e3), "unit": UNIT,
                    "h2d_bytes_per_step": 4 * (wl.N * 3 + wl.N + wl.M * 3),
                    "d2h_bytes_per_step": 4 * (wl.N + wl.N * 3)}
     plan.close()
     return out
+
+
+def separable_bytes(P: int, levels: int, grid: int) -> int:
+    """Bytes the separable M2L must move per transform: every pass reads its input rows once and
+    writes its output rows once (P values per Taylor row, C(order+4, 4) per 4-indexed row; one
+    chain of intermediates at the finest level, two above it)."""
+    order = 0
+    while (order + 1) * (order + 2) * (order + 3) // 6 < P:
+        order += 1
+    Q4 = (order + 1) * (order + 2) * (order + 3) * (order + 4) // 24
+    total = 0
+    for l in range(levels):
+        G = (grid >> l) ** 3
+        ch = 1 if l == 0 else 2
+        total += G * 4 * ((P + ch * Q4) + (ch * Q4 + ch * Q4) + (ch * Q4 + P))
+    return total
 
 
 def roofline_for(m: Measured, peaks):
@@ -324,6 +346,18 @@ def roofline_for(m: Measured, peaks):
     useful = 2 * m.info["m2l_useful_flops"]
     issued = 2 * m.info["m2l_issued_flops"]
     achieved = useful / (m2l_ms / 1e3) / 1e12
+    if m.mode == "separable":
+        hbm = peaks.get("hbm_gbs")
+        basis = "of measured hbm copy (MEASURED_PEAKS.json)"
+        if hbm is None:
+            hbm, basis = 6800.0, "of fallback hbm"
+        b = 2 * separable_bytes(m.info["coefficients"], m.info["levels"], m.grid)   # per step
+        gbs = b / (m2l_ms / 1e3) / 1e9
+        return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "traffic": M2L_TRAFFIC_BYTES.get("separable"), "traffic_unit": "bytes per transform (6 launches)",
+                "kernel": "k_m2l_sep (passes X, Y, Z; finest level and levels above it: 6 launches per transform)",
+                "bytes_per_step": b, "useful_flops_per_step": useful,
+                "useful_flops_achieved_tflops": achieved, "peak_basis": basis}
     if m.mode == "fp32":
         sm = peaks.get("sm_max_mhz", 2070.0)
         peak = fp32_peak_tflops(sm)
@@ -387,12 +421,12 @@ def run_ours(args, rank, world, local_rank):
     ref = None
     if not args.no_check and rank == 0:
         ref = oracle_reference_sample(wl)
-    primary = "bf16x3" if args.m2l == "auto" else args.m2l
+    primary = "separable" if args.m2l == "auto" else args.m2l
     main = measure_mode(primary, wl, args, world, dev, flush, ref=ref, do_e2e=not args.no_e2e, clocks=True)
     variants = {}
     if args.m2l == "auto":
-        for mode in ("tf32x3", "tf32", "bf16", "fp32"):
-            variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref)
+        for mode in ("bf16x3", "tf32x3", "tf32", "bf16", "fp32"):
+            variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref, steps=min(args.steps, 10))
     if rank != 0:
         return
     peaks = load_peaks()

@@ -136,6 +136,15 @@ FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
                             const float *q, int64_t M, const float *ybar,
                             float *wbar, float *pbar);
 
+/* Exact evaluation of Sec. 3, Eq. 1 by brute force, y[m] = sum_n psi(p[n] - q[m]) w[n], in
+ * O(N M) on the device (one thread per query, compensated FP32 summation): the sum the series
+ * approximates, for measuring a plan's truncation error on a sample of queries.  Uses
+ * desc->dim, desc->kernel (Gaussian only) and desc->sigma; no plan.  Device arrays as in
+ * fc2t2_forward; asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (polynomial
+ * kernel), CUDA. */
+FC2T2_API fc2t2_status fc2t2_direct(const fc2t2_plan_desc *desc, void *stream, const float *p, const float *w,
+                                    int64_t N, const float *q, int64_t M, float *y);
+
 /* Synchronise `stream` and report the device-side conditions raised on `plan`: TIMEOUT if a
  * bounded device-side wait of the tensor-core M2L gave up in any call since the last check (the
  * outputs of that call are then incomplete; the condition is cleared by this check), DOMAIN if
@@ -143,6 +152,18 @@ FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
  * make the same check themselves when check_domain is set.  Errors: INVALID_ARG, CUDA, and the
  * two conditions above. */
 FC2T2_API fc2t2_status fc2t2_plan_check(fc2t2_plan plan, void *stream);
+
+/* Gradient with respect to the query positions for a cotangent ybar:
+ *   qbar[m][i] = ybar[m] * d/dx_i y(x) at x = q[m],   y(x) = the forward series of (p, w)
+ * (the derivative of the local series, the binning of q held fixed -- the same reading as pbar).
+ * Sec. 4.1 derives the adjoints for p and w; the query gradient is what the paper's accessor
+ * exposes as the field's first partial derivatives (Sec. 3, "How to use the implementation?"),
+ * and what a layer whose q comes from a network needs (Sec. 4's usage example); ybar = 1 gives
+ * the field's gradient at q.  Recomputes the forward expansion.  qbar is [M][dim].
+ * Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
+FC2T2_API fc2t2_status fc2t2_backward_q(fc2t2_plan plan, void *stream,
+                                        const float *p, const float *w, int64_t N,
+                                        const float *q, int64_t M, const float *ybar, float *qbar);
 
 /* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
  * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,

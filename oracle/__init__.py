@@ -12,6 +12,7 @@ Public functions (all arrays are numpy, float64 unless stated):
 * ``backward(desc, p, w, q, ybar, sel=None, ...)`` -> (wbar, pbar)
     Sec. 4.1: wbar = f(p; q, ybar) (the transposed transform) and
     pbar = w * grad f(p; q, ybar).
+* ``backward_q(desc, p, w, q, ybar, sel=None, ...)`` -> qbar (gradient at the queries).
 * ``direct(desc, p, w, q, sel=None)`` -> exact O(NM) sum of Eq. 1.
 * ``kernel_derivs(desc, c)`` -> d^m psi(c), |m| <= order, graded order.
 * ``multi_indices(dim, order)`` -> exponents [P, dim], graded order.
@@ -216,6 +217,16 @@ def backward(desc: OracleDesc, p, w, q, ybar, sel=None, src_cell=None, tgt_cell=
                           want_grad=True, fault=fault)
     ws = w if sel is None else w[np.asarray(sel, dtype=np.int64)]
     return val, grad * ws[:, None]
+
+
+def backward_q(desc: OracleDesc, p, w, q, ybar, sel=None, src_cell=None, tgt_cell=None, fault="none"):
+    """qbar_m = ybar_m * grad_x f(x; p, w)|_{x=q_m}: the derivative of the forward local series at
+    the (selected) queries, the binning of q held fixed (as for pbar, Sec. 4.1)."""
+    ybar = _f64(ybar).reshape(-1)
+    _, grad = transform(desc, p, w, q, sel=sel, src_cell=src_cell, tgt_cell=tgt_cell, want_grad=True,
+                        fault=fault)
+    yb = ybar if sel is None else ybar[np.asarray(sel, dtype=np.int64)]
+    return grad * yb[:, None]
 
 
 def direct(desc: OracleDesc, p, w, q, sel=None):

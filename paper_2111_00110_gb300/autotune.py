@@ -1,0 +1,87 @@
+"""Per-instance choice of grid and expansion order (the batched workload's autotuner).
+
+Each candidate (grid, order, M2L form) is built as a plan and run on the instance: its time is a
+forward + backward step measured with CUDA events, its error the relative L2 distance to the exact
+sum (``fc2t2_direct``, brute force on the device) on a seeded sample of queries.  The choice is the
+fastest candidate whose error meets the target; when none does, the most accurate one.  The
+selection rule is separate from the measurements so that it can be checked on the host.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Iterable, List, Optional, Sequence, Tuple
+
+import numpy as np
+
+
+@dataclass
+class Candidate:
+    grid: int
+    order: int
+    m2l: str
+    ms: float              # forward + backward, milliseconds
+    err: float             # relative L2 error of y against the exact sum on the query sample
+
+
+def select(cands: Sequence[Candidate], target: float) -> Candidate:
+    """Fastest candidate with err <= target; if there is none, the most accurate (then fastest)."""
+    if not cands:
+        raise ValueError("no candidates")
+    ok = [c for c in cands if c.err <= target]
+    if ok:
+        return min(ok, key=lambda c: (c.ms, c.err))
+    return min(cands, key=lambda c: (c.err, c.ms))
+
+
+def _rel_l2(a, b) -> float:
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.clamp(torch.linalg.vector_norm(b), min=1e-300))
+
+
+def measure(p, w, q, sigma: float, grid: int, order: int, m2l: str, sample, ref, reps: int = 3) -> Candidate:
+    """Time a forward + backward step of one candidate and its error on the query sample."""
+    import torch
+    from .transform import Plan
+    dim = p.shape[1]
+    plan = Plan(dim, grid, order, sigma, m2l=m2l, max_sources=max(p.shape[0], 1),
+                max_queries=max(q.shape[0], 1), device=p.device)
+    try:
+        y = plan.forward(p, w, q)
+        plan.backward(p, w, q, y)
+        stream = torch.cuda.current_stream(p.device)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            y = plan.forward(p, w, q)
+            plan.backward(p, w, q, y)
+        b.record(stream)
+        torch.cuda.synchronize(p.device)
+        plan.check()
+        err = _rel_l2(y[sample], ref)
+        return Candidate(grid, order, m2l, a.elapsed_time(b) / reps, err)
+    finally:
+        plan.close()
+
+
+def autotune(p, w, q, sigma: float, target: float = 1e-2, grids: Iterable[int] = (32, 64),
+             orders: Iterable[int] = (4, 6, 8), m2l: Iterable[str] = ("separable",), sample: int = 1024,
+             seed: int = 0, reps: int = 3) -> Tuple[Candidate, List[Candidate]]:
+    """Measure every (grid, order, form) candidate on the instance (p, w, q) and choose one.
+
+    ``sample`` queries (seeded) are compared with the exact sum.  Returns (choice, all)."""
+    from .transform import direct
+    M = q.shape[0]
+    rng = np.random.default_rng(seed)
+    k = min(sample, M)
+    idx = np.sort(rng.choice(M, size=k, replace=False)) if k < M else np.arange(M)
+    import torch
+    sample_idx = torch.as_tensor(idx, device=q.device, dtype=torch.long)
+    ref = direct(p, w, q[sample_idx].contiguous(), sigma)
+    cands = [measure(p, w, q, sigma, g, o, f, sample_idx, ref, reps)
+             for g in grids for o in orders for f in m2l]
+    return select(cands, target), cands
+
+
+def tune_batch(instances, sigma: float, target: float = 1e-2, **kw) -> List[Candidate]:
+    """Choice per instance of a batch: ``instances`` yields (p, w, q) device tensors."""
+    return [autotune(p, w, q, sigma, target, **kw)[0] for p, w, q in instances]

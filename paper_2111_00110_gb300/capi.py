@@ -41,6 +41,8 @@ EXPORTS = (
     "fc2t2_backward_batched",
     "fc2t2_plan_query",
     "fc2t2_plan_check",
+    "fc2t2_direct",
+    "fc2t2_backward_q",
 )
 STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack")
 
@@ -112,6 +114,8 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_backward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fc2t2_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         lib.fc2t2_plan_check.argtypes = [vp, vp]
+        lib.fc2t2_direct.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
+        lib.fc2t2_backward_q.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
@@ -146,6 +150,15 @@ def forward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, y: i
 def backward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int,
              wbar: int, pbar: int) -> None:
     check(load().fc2t2_backward(plan, stream, p, w, N, q, M, ybar, wbar, pbar))
+
+
+def backward_q(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int, qbar: int) -> None:
+    check(load().fc2t2_backward_q(plan, stream, p, w, N, q, M, ybar, qbar))
+
+
+def direct(desc: PlanDesc, stream: int, p: int, w: int, N: int, q: int, M: int, y: int) -> None:
+    """Brute-force sum of Eq. 1 on the device (device pointers)."""
+    check(load().fc2t2_direct(ctypes.byref(desc), stream, p, w, N, q, M, y))
 
 
 def plan_check(plan: int, stream: int) -> None:

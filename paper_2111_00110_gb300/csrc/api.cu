@@ -496,6 +496,33 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     return finish_flags(pl, s);
 }
 
+fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                              const float *q, int64_t M, const float *ybar, float *qbar) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (N < 0 || M < 0 || N > pl->src.cap || M > pl->qry.cap)
+        return set_error(FC2T2_ERR_INVALID_ARG, "N or M outside [0, max]");
+    if (M == 0) return FC2T2_OK;
+    if (!q || !ybar || !qbar || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    fc2t2_status st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if (N == 0) {
+        if ((st = check_cuda(cudaMemsetAsync(qbar, 0, sizeof(float) * M * pl->D, s), "zero qbar")) != FC2T2_OK) return st;
+        if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
+        return finish_flags(pl, s);
+    }
+    // the forward expansion of (p, w), its local series differentiated at q, times ybar
+    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
+    if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, nullptr, qbar), "l2p grad at queries")) != FC2T2_OK)
+            return st;
+    }
+    return finish_flags(pl, s);
+}
+
 fc2t2_status fc2t2_plan_check(fc2t2_plan pl, void *stream) {
     if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
     return read_flags(pl, static_cast<cudaStream_t>(stream), true);

@@ -1,5 +1,6 @@
 // Separable M2L for the Gaussian kernel (Sec. 3: M2L as a convolution over the parity window;
-// the Gaussian's derivative table factors per dimension).
+// Sec. 3, future work on decomposable kernels: chained one-dimensional convolutions when the
+// kernel's derivatives factor per dimension, as the Gaussian's do).
 //
 // With Dt_o(m) = prod_i dt_{o_i}(m_i), dt_o(j) = h^j g^(j)(o h) the scaled 1D derivatives, the
 // M2L of one level
@@ -122,7 +123,7 @@ template <int RHO, int R, int SET>
 __device__ __forceinline__ void sep_accum_y(float (&acc)[tri_count(R)], const float *inb, int tl, int par, int gin,
                                             const float *s_dt) {
     constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
-#pragma unroll 1
+#pragma unroll 1   // (unrolled, the budget-specialised bodies overflow the instruction cache)
     for (int o = 0; o < 7; ++o) {
         if (!in_set(SET, o - 3)) continue;
         const bool ex = excluded(o - 3, par);
@@ -162,22 +163,23 @@ __device__ __forceinline__ void sep_store_y(float (&acc)[tri_count(R)], float *o
     }
 }
 
-// pass Y, task (t, kx, bz).  Finest level: the window on in0.  Above it, chain 0 (U) = the
-// window on in0 plus the window minus the hole on in1, chain 1 (V) = the hole on in1.
+// pass Y, task (t, kx, bz), one chain.  Finest level: the window on in0.  Above it (the chains
+// are computed one after the other into the same shared-memory rows), chain 0 (U) = the window
+// on in0 plus the window minus the hole on in1, chain 1 (V) = the hole on in1.
 template <int RHO, int R, bool FINEST>
 __device__ __forceinline__ void sep_task_y(const float *in0, const float *in1, int tl, int par, int kx, int bz,
-                                           const float *s_dt, const int *s_goff, float *out0, float *out1) {
+                                           const float *s_dt, const int *s_goff, float *out, int chain) {
     const int gin = s_goff[kx * (RHO + 1) + bz];
     float acc[tri_count(R)];
 #pragma unroll
     for (int i = 0; i < tri_count(R); ++i) acc[i] = 0.0f;
-    sep_accum_y<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
-    if (!FINEST) sep_accum_y<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
-    sep_store_y<RHO, R>(acc, out0, kx, bz, s_goff);
-    if (!FINEST) {
+    if (chain == 0) {
+        sep_accum_y<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
+        if (!FINEST) sep_accum_y<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
+    } else {
         sep_accum_y<RHO, R, kSetH>(acc, in1, tl, par, gin, s_dt);
-        sep_store_y<RHO, R>(acc, out1, kx, bz, s_goff);
     }
+    sep_store_y<RHO, R>(acc, out, kx, bz, s_goff);
 }
 
 // pass Z: adds sum_{oz in SET} sum_{bz} dt_oz(kz+bz) T2[t+oz](kx, ky, bz, f = kz) into acc(kz)
@@ -185,7 +187,7 @@ template <int RHO, int R, int SET>
 __device__ __forceinline__ void sep_accum_z(float (&acc)[R + 1], const float *inb, int tl, int par, int gin,
                                             const float *s_dt) {
     constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
-#pragma unroll 1
+#pragma unroll
     for (int o = 0; o < 7; ++o) {
         if (!in_set(SET, o - 3)) continue;
         const bool ex = excluded(o - 3, par);
@@ -222,9 +224,9 @@ __device__ __forceinline__ void sep_task_z(const float *in0, const float *in1, i
 
 template <int RHO, int AXIS, bool FINEST, int R>
 __device__ __forceinline__ void sep_task(const float *in0, const float *in1, int tl, int par, int2 pr,
-                                         const float *s_dt, const int *s_goff, float *out0, float *out1) {
+                                         const float *s_dt, const int *s_goff, float *out0, float *out1, int chain) {
     if (AXIS == 0) sep_task_x<RHO, R, FINEST>(in0, tl, par, pr.x, pr.y, s_dt, s_goff, out0, out1);
-    else if (AXIS == 1) sep_task_y<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0, out1);
+    else if (AXIS == 1) sep_task_y<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0, chain);
     else sep_task_z<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0);
 }
 
@@ -240,12 +242,18 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     constexpr int P = ncoef(3, RHO);
     constexpr int T2 = tri_count(RHO);          // (i, j) pairs with i + j <= rho
     using Pt = SepPitch<RHO, AXIS>;
-    constexpr bool TWO_IN = !FINEST && AXIS > 0, TWO_OUT = !FINEST && AXIS < 2;
+    constexpr bool TWO_IN = !FINEST && AXIS > 0;
+    constexpr bool TWO_OUT = !FINEST && AXIS == 0;       // pass X fills both chains at once
+    constexpr int NCHAIN = (!FINEST && AXIS == 1) ? 2 : 1;   // pass Y: one chain after the other
     extern __shared__ float sm[];
+    // the finest level is launched alone (its tables at compile-time offsets); the levels above
+    // it share a launch, blocks ordered level by level
     int lvl = 0;
+    if (!FINEST) {
 #pragma unroll
-    for (int i = 1; i < kMaxLevels; ++i)
-        if (i < args.nlev && (int)blockIdx.x >= args.lv[i].block0) lvl = i;
+        for (int i = 1; i < kMaxLevels; ++i)
+            if (i < args.nlev && (int)blockIdx.x >= args.lv[i].block0) lvl = i;
+    }
     const SepLevel lv = args.lv[lvl];
     const int n = lv.n;
     const int bl = (int)blockIdx.x - lv.block0;
@@ -305,50 +313,55 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     }
     __syncthreads();
 
-    for (int task = threadIdx.x; task < nt * T2; task += blockDim.x) {
-        const int tl = task % nt;
-        const int2 pr = s_pair[task / nt];
-        const int par = (t0 + tl) & 1;
-        float *o0 = out0 + tl * Pt::sout, *o1 = out1 + tl * Pt::sout;
-        // the lanes of a warp share the task's pair (and so its budget) when a segment has 32 cells
-        switch (RHO - pr.x - pr.y) {
+#pragma unroll 1
+    for (int chain = 0; chain < NCHAIN; ++chain) {
+        for (int task = threadIdx.x; task < nt * T2; task += blockDim.x) {
+            const int tl = task % nt;
+            const int2 pr = s_pair[task / nt];
+            const int par = (t0 + tl) & 1;
+            float *o0 = out0 + tl * Pt::sout, *o1 = out1 + tl * Pt::sout;
+            // the lanes of a warp share the task's pair (and so its budget) when a segment has 32 cells
+            switch (RHO - pr.x - pr.y) {
 #define FC2T2_SEP_R(R_)                                                                                 \
     case R_:                                                                                            \
         if constexpr (R_ <= RHO)                                                                        \
-            sep_task<RHO, AXIS, FINEST, R_>(in0, in1, tl, par, pr, s_dt, s_goff, o0, o1);              \
+            sep_task<RHO, AXIS, FINEST, R_>(in0, in1, tl, par, pr, s_dt, s_goff, o0, o1, chain);       \
         break;
-            FC2T2_SEP_R(0) FC2T2_SEP_R(1) FC2T2_SEP_R(2) FC2T2_SEP_R(3) FC2T2_SEP_R(4)
-            FC2T2_SEP_R(5) FC2T2_SEP_R(6) FC2T2_SEP_R(7) FC2T2_SEP_R(8)
+                FC2T2_SEP_R(0) FC2T2_SEP_R(1) FC2T2_SEP_R(2) FC2T2_SEP_R(3) FC2T2_SEP_R(4)
+                FC2T2_SEP_R(5) FC2T2_SEP_R(6) FC2T2_SEP_R(7) FC2T2_SEP_R(8)
 #undef FC2T2_SEP_R
-            default: break;
-        }
-    }
-    __syncthreads();
-
-    // write the segment's output rows, a warp per row (padding columns of Lt rows are zero;
-    // padding of the 4-indexed rows is never read)
-    {
-        constexpr int W = kSepThreads / 32, CPL = (Pt::out + 31) / 32;
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-#pragma unroll 1
-        for (int rr = warp; rr < nt; rr += W) {
-            float *g0 = lv.out0 + (base + (int64_t)(t0 + rr) * stride) * Pt::out;
-            const float *s0 = out0 + rr * Pt::sout;
-#pragma unroll
-            for (int k = 0; k < CPL; ++k) {
-                const int c = lane + 32 * k;
-                if (c < Pt::out) g0[c] = (AXIS == 2 && c >= P) ? 0.0f : s0[c];
+                default: break;
             }
-            if (TWO_OUT) {
-                float *g1 = lv.out1 + (base + (int64_t)(t0 + rr) * stride) * Pt::out;
-                const float *s1 = out1 + rr * Pt::sout;
+        }
+        __syncthreads();
+
+        // write the segment's output rows, a warp per row (padding columns of Lt rows are zero;
+        // padding of the 4-indexed rows is never read)
+        {
+            constexpr int W = kSepThreads / 32, CPL = (Pt::out + 31) / 32;
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            float *gout0 = chain == 0 ? lv.out0 : lv.out1;
+#pragma unroll 1
+            for (int rr = warp; rr < nt; rr += W) {
+                float *g0 = gout0 + (base + (int64_t)(t0 + rr) * stride) * Pt::out;
+                const float *s0 = out0 + rr * Pt::sout;
 #pragma unroll
                 for (int k = 0; k < CPL; ++k) {
                     const int c = lane + 32 * k;
-                    if (c < Pt::out) g1[c] = s1[c];
+                    if (c < Pt::out) g0[c] = (AXIS == 2 && c >= P) ? 0.0f : s0[c];
+                }
+                if (TWO_OUT) {
+                    float *g1 = lv.out1 + (base + (int64_t)(t0 + rr) * stride) * Pt::out;
+                    const float *s1 = out1 + rr * Pt::sout;
+#pragma unroll
+                    for (int k = 0; k < CPL; ++k) {
+                        const int c = lane + 32 * k;
+                        if (c < Pt::out) g1[c] = s1[c];
+                    }
                 }
             }
         }
+        if (NCHAIN > 1) __syncthreads();   // the next chain reuses the output rows
     }
 }
 
@@ -357,7 +370,9 @@ namespace {
 // shared memory of one CTA of a pass for `seg` target cells
 size_t sep_smem(int axis, int seg, bool finest, int in_pitch, int out_pitch) {
     const int nin = seg + 6;
-    const bool two = !finest && axis > 0, two_out = !finest && axis < 2;
+    // two input chains above the finest level (passes Y, Z); two output rows per cell only for
+    // pass X (pass Y computes its two chains one after the other into the same rows)
+    const bool two = !finest && axis > 0, two_out = !finest && axis == 0;
     const size_t f = (size_t)nin * odd_pitch(in_pitch) * (two ? 2 : 1) +
                      (size_t)seg * odd_pitch(out_pitch) * (two_out ? 2 : 1);
     return f * sizeof(float);

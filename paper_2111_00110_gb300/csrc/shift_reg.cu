@@ -1,4 +1,4 @@
-// M2M and L2L with the re-centring done in registers, one thread per cell (orders <= 6).
+// M2M and L2L with the re-centring done in registers (every order up to 8).
 //
 // Re-centring a degree-rho polynomial by a per-dimension offset factorises over dimensions
 // (Sec. 3: the M2M and L2L kernels are products of one-dimensional binomial shifts), and the
@@ -7,9 +7,10 @@
 //   moments (M2M):  a(..., n_d, ...) += sum_{k_d < n_d} t(n_d - k_d) a(..., k_d, ...)   (n_d descending)
 //   locals  (L2L):  a(..., k_d, ...) += sum_{g_d > k_d} t(g_d - k_d) a(..., g_d, ...)   (k_d ascending)
 // with t(j) = s^j / j!, s = +-1/2 the child centre's offset from the parent centre in child
-// cell widths.  M2M: a parent thread loads each child row, shifts it and accumulates, then
-// scales by 2^-|a|.  L2L: a child thread loads its parent row, scales by 2^-|g|, shifts it and
-// adds it to its own row.  Rows move as 16-byte loads and stores.
+// cell widths.  M2M: a parent thread (large levels) or the parent's 2^D child threads (small
+// levels, summing by warp shuffles) shift the child rows and scale the sum by 2^-|a|.  L2L: a
+// child thread loads its parent row, scales by 2^-|g|, shifts it and adds it to its own row.
+// Rows move as 16-byte loads.
 #include "dispatch.cuh"
 #include "fc2t2_internal.cuh"
 
@@ -92,6 +93,7 @@ __device__ __forceinline__ float pow2_neg_deg(int k) {
     return 1.0f / (float)(1 << d);
 }
 
+// M2M at large levels: one thread per parent cell, its children loaded and shifted in turn.
 template <int D, int RHO>
 __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, float *__restrict__ Mp, int np,
                                                  int64_t Gp) {
@@ -127,6 +129,52 @@ __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, f
     store_row<D, RHO>(Mp + C * Pp, acc);
 }
 
+// M2M at small levels: one thread per child cell, the 2^D children of a parent in consecutive
+// lanes (at a few thousand parents one thread per parent leaves the GPU idle).  Each
+// thread re-centres its child's row in registers; the parent's row is the sum over its lanes
+// (butterfly shuffles), scaled by 2^-|a|; lane ch then writes the coefficients k = ch mod 2^D.
+template <int D, int RHO>
+__global__ void __launch_bounds__(256) k_m2m_child(const float *__restrict__ Mc, float *__restrict__ Mp, int np,
+                                                 int64_t Gp) {
+    constexpr int P = ncoef(D, RHO), Pp = pad4(P), NCH = 1 << D;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t C = t >> D;
+    const int ch = (int)(t & (NCH - 1));
+    const bool valid = C < Gp;
+    float a[P];
+    if (valid) {
+        int cp[3] = {0, 0, 0};
+        int64_t r = C;
+        for (int d = 0; d < D; ++d) { cp[d] = (int)(r % np); r /= np; }
+        const int nl = 2 * np;
+        int64_t lin = 0;
+        for (int d = D - 1; d >= 0; --d) lin = lin * nl + (2 * cp[d] + ((ch >> d) & 1));
+        load_row<D, RHO>(Mc + lin * Pp, a);
+#pragma unroll
+        for (int d = 0; d < D; ++d) shift_axis<D, RHO, true>(a, d, ((ch >> d) & 1) ? 0.5f : -0.5f);
+    } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) a[k] = 0.0f;
+    }
+    // every lane of the warp takes part in the shuffles (invalid lanes add zeros)
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+#pragma unroll
+        for (int off = 1; off < NCH; off <<= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+    if (!valid) return;
+    float *dst = Mp + C * Pp;
+#pragma unroll
+    for (int dg = 0; dg <= RHO; ++dg) {
+        const float sc = 1.0f / (float)(1 << dg);
+#pragma unroll
+        for (int k = (dg == 0 ? 0 : ncoef(D, dg - 1)); k < ncoef(D, dg); ++k)
+            if ((k & (NCH - 1)) == ch) dst[k] = a[k] * sc;
+    }
+#pragma unroll
+    for (int k = P; k < Pp; ++k)
+        if ((k & (NCH - 1)) == ch) dst[k] = 0.0f;
+}
+
 template <int D, int RHO>
 __global__ void __launch_bounds__(128) k_l2l_reg(const float *__restrict__ Lp, float *__restrict__ Lc, int nl,
                                                  int64_t Gc) {
@@ -151,26 +199,43 @@ __global__ void __launch_bounds__(128) k_l2l_reg(const float *__restrict__ Lp, f
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) shift_axis<D, RHO, false>(a, d, (cc[d] & 1) ? 0.5f : -0.5f);
-    float own[P];
-    load_row<D, RHO>(Lc + c * Pp, own);
+    // add into the child's own row in 16-byte chunks (only the shifted parent row stays live)
+    float4 *own = reinterpret_cast<float4 *>(Lc + c * Pp);
 #pragma unroll
-    for (int k = 0; k < P; ++k) own[k] += a[k];
-    store_row<D, RHO>(Lc + c * Pp, own);
+    for (int i = 0; i < Pp / 4; ++i) {
+        float4 v = own[i];
+        if (4 * i < P) v.x += a[4 * i];
+        if (4 * i + 1 < P) v.y += a[4 * i + 1];
+        if (4 * i + 2 < P) v.z += a[4 * i + 2];
+        if (4 * i + 3 < P) v.w += a[4 * i + 3];
+        own[i] = v;
+    }
 }
 
 template <int D, int RHO>
 cudaError_t run_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
-    if constexpr (RHO <= 6) {
+    {
         const Level &c = pl->lev[level], &p = pl->lev[level + 1];
-        const unsigned blocks = (unsigned)((p.G + 127) / 128);
-        k_m2m_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G);
+        // the per-parent form holds two rows in registers: orders <= 6 only
+        bool done = false;
+        if constexpr (RHO <= 6) {
+            if (p.G > 4096) {
+                const unsigned blocks = (unsigned)((p.G + 127) / 128);
+                k_m2m_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G);
+                done = true;
+            }
+        }
+        if (!done) {
+            const unsigned blocks = (unsigned)((p.G * (1 << D) + 255) / 256);
+            k_m2m_child<D, RHO><<<blocks, 256, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G);
+        }
     }
     return cudaGetLastError();
 }
 
 template <int D, int RHO>
 cudaError_t run_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
-    if constexpr (RHO <= 6) {
+    {
         const Level &p = pl->lev[level + 1], &c = pl->lev[level];
         const unsigned blocks = (unsigned)((c.G + 127) / 128);
         k_l2l_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_L + p.off * pl->Pp, pl->d_L + c.off * pl->Pp, c.n, c.G);
@@ -179,14 +244,12 @@ cudaError_t run_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
 }
 
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err) {
-    if (pl->rho > 6) return false;
     pl->launches[FC2T2_STAGE_M2M] += 1;
     FC2T2_DISPATCH(pl->D, pl->rho, (err = run_m2m_reg<D_, R_>(pl, s, level)), return false)
     return true;
 }
 
 bool launch_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err) {
-    if (pl->rho > 6) return false;
     pl->launches[FC2T2_STAGE_L2L] += 1;
     FC2T2_DISPATCH(pl->D, pl->rho, (err = run_l2l_reg<D_, R_>(pl, s, level)), return false)
     return true;

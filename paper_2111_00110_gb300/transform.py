@@ -120,8 +120,21 @@ class Plan:
         return wbar, pbar
 
 
+    def backward_q(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, ybar: torch.Tensor) -> torch.Tensor:
+        """qbar[m] = ybar[m] * grad y(q[m]) (the derivative of the local series at the queries)."""
+        N, M = p.shape[0], q.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", (N,))
+        _check_tensor(q, "q", (M, self.dim))
+        _check_tensor(ybar, "ybar", (M,))
+        qbar = torch.empty(M, self.dim, device=q.device, dtype=torch.float32)
+        capi.backward_q(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar), _ptr(qbar))
+        return qbar
+
+
 class FC2T2Function(torch.autograd.Function):
-    """y = f(q; p, w) with hand-written adjoints (Sec. 4.1); q is treated as data."""
+    """y = f(q; p, w) with hand-written adjoints (Sec. 4.1); the query gradient is computed when
+    q requires it."""
 
     @staticmethod
     def forward(ctx, p, w, q, plan: Plan):
@@ -133,16 +146,35 @@ class FC2T2Function(torch.autograd.Function):
     @staticmethod
     def backward(ctx, ybar):
         p, w, q = ctx.saved_tensors
-        need_p, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
-        if not (need_p or need_w):
-            return None, None, None, None
-        wbar, pbar = ctx.plan.backward(p, w, q, ybar.contiguous(), need_w=need_w, need_p=need_p)
-        return pbar, wbar, None, None
+        need_p, need_w, need_q = ctx.needs_input_grad[0], ctx.needs_input_grad[1], ctx.needs_input_grad[2]
+        ybar = ybar.contiguous()
+        wbar = pbar = qbar = None
+        if need_p or need_w:
+            wbar, pbar = ctx.plan.backward(p, w, q, ybar, need_w=need_w, need_p=need_p)
+        if need_q:
+            qbar = ctx.plan.backward_q(p, w, q, ybar)
+        return pbar, wbar, qbar, None
 
 
 def fc2t2(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable explicit layer y = f(q; p, w) (Sec. 4)."""
     return FC2T2Function.apply(p, w, q, plan)
+
+
+def direct(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, sigma: float) -> torch.Tensor:
+    """Exact y[m] = sum_n exp(-|p[n] - q[m]|^2 / (2 sigma^2)) w[n] by brute force on the device
+    (O(N M); for error measurements on query samples)."""
+    dim = p.shape[1]
+    N, M = p.shape[0], q.shape[0]
+    _check_tensor(p, "p", (N, dim))
+    _check_tensor(w, "w", (N,))
+    _check_tensor(q, "q", (M, dim))
+    d = capi.PlanDesc()
+    d.dim, d.grid, d.order, d.kernel, d.sigma = dim, 4, 1, capi.KERNELS["gaussian"], float(sigma)
+    d.lo, d.hi, d.channels = 0.0, 1.0, 1
+    y = torch.empty(M, device=q.device, dtype=torch.float32)
+    capi.direct(d, torch.cuda.current_stream(q.device).cuda_stream, _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(y))
+    return y
 
 
 def forward_batched(plans: Sequence[Plan], ps, ws, qs):

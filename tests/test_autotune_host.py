@@ -1,0 +1,30 @@
+"""The autotuner's selection rule (host logic, no GPU)."""
+import pytest
+
+from paper_2111_00110_gb300.autotune import Candidate, select
+
+
+def C(g, o, ms, err):
+    return Candidate(g, o, "separable", ms, err)
+
+
+def test_fastest_within_target():
+    cands = [C(32, 4, 1.0, 3e-2), C(32, 6, 1.5, 8e-3), C(64, 4, 2.0, 9e-3), C(64, 8, 4.0, 1e-4)]
+    assert select(cands, 1e-2) == cands[1]
+    assert select(cands, 1e-3) == cands[3]
+    assert select(cands, 1.0) == cands[0]
+
+
+def test_none_within_target_takes_the_most_accurate():
+    cands = [C(32, 4, 1.0, 3e-2), C(32, 6, 0.5, 2e-2), C(64, 6, 2.0, 2e-2)]
+    assert select(cands, 1e-3) == cands[1]   # most accurate, ties broken by time
+
+
+def test_ties_in_time_prefer_accuracy():
+    cands = [C(32, 6, 1.0, 5e-3), C(64, 4, 1.0, 1e-3)]
+    assert select(cands, 1e-2) == cands[1]
+
+
+def test_empty():
+    with pytest.raises(ValueError):
+        select([], 1e-2)

@@ -196,3 +196,32 @@ def test_fit_loop_small(lib):
     assert losses[-1] < 0.8 * losses[0], losses
     assert all(b <= a for a, b in zip(losses[1:], losses[2:])), losses
     plan.close()
+
+
+# ------------------------------------------------------------------ exact sum, autotuner
+
+def test_direct_sum_matches_the_oracle(lib):
+    """The brute-force device sum of Eq. 1 against the oracle's exact sum."""
+    from paper_2111_00110_gb300.transform import direct
+    for dim in (2, 3):
+        wl = workloads.uniform(71 + dim, dim, 20000, 3000, 16, 4, 0.05)
+        y = direct(dev(wl.p), dev(wl.w), dev(wl.q), wl.sigma)
+        torch.cuda.synchronize()
+        yo = oracle.direct(odesc(dim, 16, 4, wl.sigma), *f64(wl.p, wl.w, wl.q))
+        assert rel_l2(y.cpu().numpy(), yo) <= 1e-6
+
+
+def test_autotune_meets_the_target_on_a_batch_instance(lib):
+    """Grid and order chosen per instance: the choice meets the error target against the exact
+    sum and is the fastest candidate that does."""
+    from paper_2111_00110_gb300.autotune import autotune
+    wl = workloads.mixture(3, n_override=30000)
+    choice, cands = autotune(dev(wl.p), dev(wl.w), dev(wl.q), 0.02, target=1e-2, grids=(32, 64),
+                             orders=(4, 6, 8), sample=512)
+    print([(c.grid, c.order, round(c.ms, 3), f"{c.err:.2e}") for c in cands], "->", (choice.grid, choice.order))
+    assert len(cands) == 6
+    assert choice.err <= 1e-2
+    assert choice.ms == min(c.ms for c in cands if c.err <= 1e-2)
+    # the error falls with the order on the finer grid (truncation, Sec. 3)
+    errs = {(c.grid, c.order): c.err for c in cands}
+    assert errs[(64, 8)] < errs[(64, 4)]

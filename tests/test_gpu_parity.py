@@ -316,3 +316,35 @@ def test_tensor_core_m2l_backward(lib, mode):
     rel, elem = TC_BARS[mode]
     assert_close(wbar, wo, rel=rel, elem=elem, what=f"{mode} wbar")
     assert_close(pbar, po, rel=rel, elem=elem, what=f"{mode} pbar")
+
+
+# ------------------------------------------------------------------------ query gradient
+
+@pytest.mark.parametrize("m2l", ["fp32", "separable", "bf16x3"])
+def test_query_gradient(lib, m2l):
+    """qbar = ybar * grad y(q) through fc2t2_backward_q against the oracle (3D, 16^3, order 6)."""
+    wl = workloads.uniform(779, 3, 5000, 4000, 16, 6, 0.08)
+    ybar = wl.ybar()
+    plan = make_plan(3, 16, 6, wl.sigma, wl.N, wl.M, m2l=m2l)
+    P_, W_, Q_, YB = to_dev(wl.p, wl.w, wl.q, ybar)
+    qbar = plan.backward_q(P_, W_, Q_, YB)
+    torch.cuda.synchronize()
+    plan.check()
+    qo = oracle.backward_q(odesc(3, 16, 6, wl.sigma), *f64(wl.p, wl.w, wl.q, ybar))
+    assert_close(qbar.cpu().numpy(), qo, what=f"qbar ({m2l})")
+
+
+def test_autograd_query_gradient(lib):
+    """The autograd layer returns qbar when q requires a gradient (and pbar, wbar as before)."""
+    from paper_2111_00110_gb300.transform import fc2t2
+    wl = workloads.uniform(780, 2, 3000, 2500, 32, 4, 0.05)
+    plan = make_plan(2, 32, 4, wl.sigma, wl.N, wl.M)
+    P_, W_, Q_ = [t.requires_grad_(True) for t in to_dev(wl.p, wl.w, wl.q)]
+    y = fc2t2(P_, W_, Q_, plan)
+    (y * y).sum().backward()
+    torch.cuda.synchronize()
+    d = odesc(2, 32, 4, wl.sigma)
+    yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q))
+    qo = oracle.backward_q(d, *f64(wl.p, wl.w, wl.q, 2.0 * y.detach().cpu().numpy()))
+    assert_close(Q_.grad.cpu().numpy(), qo, what="autograd qbar")
+    assert rel_l2(y.detach().cpu().numpy(), yo) <= 1e-5

@@ -268,6 +268,32 @@ def test_gradients_vs_central_differences(dim):
             assert abs(vals[1] - pbar[n, i]) <= 2e-5 * scale
 
 
+@pytest.mark.parametrize("dim", [2, 3])
+def test_query_gradient_vs_central_differences(dim):
+    """qbar = ybar * grad_x y(x)|_{x=q} (binning of q frozen) against central differences of
+    L = sum(y^2) in the query positions; a mistake in the derivative of the local series (an
+    index shift, a missing 1/h) fails it."""
+    grid, order = (16, 4) if dim == 2 else (8, 4)
+    p, w, q = small_inputs(90 + dim, dim, 30, 40)
+    d = oracle.OracleDesc(dim=dim, grid=grid, order=order, sigma=0.12)
+    pc = oracle.bin_cells(d, p)
+    qc = oracle.bin_cells(d, q)
+    L0, y = _loss(d, p, w, q, pc, qc)
+    qbar = oracle.backward_q(d, p, w, q, 2.0 * y, src_cell=pc, tgt_cell=qc)
+    rng = np.random.default_rng(11)
+    for m in rng.choice(q.shape[0], size=6, replace=False):
+        for i in range(dim):
+            vals = []
+            for eps in (1e-3, 1e-4):
+                qp, qm = q.copy(), q.copy()
+                qp[m, i] += eps
+                qm[m, i] -= eps
+                vals.append((_loss(d, p, w, qp, pc, qc)[0] - _loss(d, p, w, qm, pc, qc)[0]) / (2 * eps))
+            scale = abs(qbar[m, i]) + 1e-3 * np.sqrt(L0) / d.sigma
+            assert abs(vals[0] - qbar[m, i]) <= 2e-3 * scale
+            assert abs(vals[1] - qbar[m, i]) <= 2e-5 * scale
+
+
 def test_truncation_error_decays_with_order():
     wl = workloads.uniform2d()
     p = wl.p.astype(np.float64)
