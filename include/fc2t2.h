@@ -153,6 +153,17 @@ FC2T2_API fc2t2_status fc2t2_direct(const fc2t2_plan_desc *desc, void *stream, c
  * two conditions above. */
 FC2T2_API fc2t2_status fc2t2_plan_check(fc2t2_plan plan, void *stream);
 
+/* fc2t2_backward after a forward call on the same plan with the same p, w, q arrays (same
+ * pointers and sizes, contents unchanged -- what an autograd layer guarantees for its saved
+ * inputs): reuses that call's sorts of p and q instead of sorting again (the cotangent is
+ * gathered into the existing order of q).  The plan checks that its sorts were made from these
+ * pointers and sizes and otherwise runs fc2t2_backward; it cannot see changed contents, which is
+ * the caller's promise.  Same results and errors as fc2t2_backward. */
+FC2T2_API fc2t2_status fc2t2_backward_reuse(fc2t2_plan plan, void *stream,
+                                            const float *p, const float *w, int64_t N,
+                                            const float *q, int64_t M, const float *ybar,
+                                            float *wbar, float *pbar);
+
 /* Gradient with respect to the query positions for a cotangent ybar:
  *   qbar[m][i] = ybar[m] * d/dx_i y(x) at x = q[m],   y(x) = the forward series of (p, w)
  * (the derivative of the local series, the binning of q held fixed -- the same reading as pbar).

@@ -43,6 +43,7 @@ EXPORTS = (
     "fc2t2_plan_check",
     "fc2t2_direct",
     "fc2t2_backward_q",
+    "fc2t2_backward_reuse",
 )
 STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack")
 
@@ -116,6 +117,7 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_plan_check.argtypes = [vp, vp]
         lib.fc2t2_direct.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
         lib.fc2t2_backward_q.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp]
+        lib.fc2t2_backward_reuse.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
@@ -150,6 +152,11 @@ def forward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, y: i
 def backward(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int,
              wbar: int, pbar: int) -> None:
     check(load().fc2t2_backward(plan, stream, p, w, N, q, M, ybar, wbar, pbar))
+
+
+def backward_reuse(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int, wbar: int,
+                   pbar: int) -> None:
+    check(load().fc2t2_backward_reuse(plan, stream, p, w, N, q, M, ybar, wbar, pbar))
 
 
 def backward_q(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int, qbar: int) -> None:

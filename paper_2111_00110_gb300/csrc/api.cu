@@ -343,7 +343,13 @@ static fc2t2_status sort_points(fc2t2_plan_s *pl, cudaStream_t s, const float *x
     fc2t2_status st;
     if ((st = check_cuda(launch_bin_count(pl, s, x, n, w), "bin")) != FC2T2_OK) return st;
     if ((st = check_cuda(launch_scan(pl, s, w.count, w.start, pl->lev[0].G), "scan")) != FC2T2_OK) return st;
-    return check_cuda(launch_scatter(pl, s, x, wt, n, w), "scatter");
+    w.held_x = nullptr;
+    w.held_n = -1;
+    if ((st = check_cuda(launch_scatter(pl, s, x, wt, n, w), "scatter")) != FC2T2_OK) return st;
+    w.held_x = x;
+    w.held_w = wt;
+    w.held_n = n;
+    return FC2T2_OK;
 }
 
 // P2M .. L2L: expansion of sorted sources into finest-level local coefficients d_L (level 0)
@@ -489,6 +495,30 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
     if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar, pbar), "l2p grad")) != FC2T2_OK) return st;
+    }
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_backward_reuse(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                                  const float *q, int64_t M, const float *ybar, float *wbar, float *pbar) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    // the plan's workspaces must hold the forward's sorts of exactly these arrays
+    const bool reuse = N > 0 && M > 0 && (wbar || pbar) && p && w && q && ybar &&
+                       pl->src.held_x == p && pl->src.held_w == w && pl->src.held_n == N &&
+                       pl->qry.held_x == q && pl->qry.held_n == M;
+    if (!reuse) return fc2t2_backward(pl, stream, p, w, N, q, M, ybar, wbar, pbar);
+    cudaStream_t s = (cudaStream_t)stream;
+    fc2t2_status st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    // the transposed transform on the existing sorts: q becomes the sources with weights ybar
+    {
+        StageScope scope(pl, s, FC2T2_STAGE_SORT);
+        if ((st = check_cuda(launch_reweight(pl, s, ybar, M, pl->qry), "reweight")) != FC2T2_OK) return st;
+    }
+    if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
     {
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
         if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar, pbar), "l2p grad")) != FC2T2_OK) return st;

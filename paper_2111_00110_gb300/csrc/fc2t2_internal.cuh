@@ -69,6 +69,9 @@ struct SortWork {
     int *rank = nullptr;        // [cap]  position of point i within its cell
     int *perm = nullptr;        // [cap]  sorted position -> input index
     float4 *rec = nullptr;      // [cap]  sorted point: (x0, x1, x2 or 0, weight or 0)
+    // what the workspace holds: the points and weights arrays (and count) it last sorted
+    const float *held_x = nullptr, *held_w = nullptr;
+    int64_t held_n = -1;
 };
 
 struct Level {
@@ -154,6 +157,7 @@ fc2t2_status check_cuda(cudaError_t e, const char *what);
 cudaError_t launch_bin_count(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, int64_t n,
                              SortWork &w);
 cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n);
+cudaError_t launch_reweight(const fc2t2_plan_s *pl, cudaStream_t s, const float *wt, int64_t n, SortWork &w);
 cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt,
                            int64_t n, SortWork &w);
 cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, float *M0);

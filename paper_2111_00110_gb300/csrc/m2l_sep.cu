@@ -452,8 +452,7 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
 
 // The launch's small tables: each level's dt_o(j); the group offsets of the 4-indexed rows; the
 // task pairs (i, j) by descending cost (ascending i + j), dealt to the kSepThreads / 32 warps
-// in a snake order (0, 1, .., W-1, W-1, .., 0, ...) so that with 32-cell segments (one pair per
-// warp and task round) every warp gets a similar share of the work.
+// in a snake order (0, 1, .., W-1, W-1, .., 0, ...) so that every warp gets a similar share.
 static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_end) {
     const int rho = pl->rho;
     for (int l = l_begin; l < l_end; ++l)
@@ -467,15 +466,26 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
                     if (x < i0 || (x == i0 && y < i1)) off += tri_count(rho - x - y);
             a.goff[i0 * (rho + 1) + i1] = off;
         }
+    // with segments of nt < 32 cells a warp's lanes cover G = 32 / nt consecutive task slots:
+    // consecutive pairs of the cost order (mostly of equal budget) go to the same warp, so its
+    // lane groups run the same specialised body
     const int T2 = tri_count(rho);
     constexpr int W = kSepThreads / 32;
+    const int seg = pl->sep.seg[l_begin];
+    const int G = seg >= 32 ? 1 : 32 / seg;
+    std::vector<int> used(T2, 0);
     int k = 0;
     for (int d = 0; d <= rho; ++d)
         for (int i = 0; i <= d; ++i) {
-            const int round = k / W, pos = k % W;
+            const int m = k / G, round = m / W, pos = m % W;
             const int w = (round & 1) ? W - 1 - pos : pos;
-            const int slot = round * W + w;
-            a.pair[slot < T2 ? slot : k] = make_int2(i, d - i);   // the partial last round keeps k
+            int slot = round * G * W + G * w + k % G;
+            if (slot >= T2) {   // the partial last round: the first free slot
+                slot = 0;
+                while (used[slot]) ++slot;
+            }
+            used[slot] = 1;
+            a.pair[slot] = make_int2(i, d - i);
             ++k;
         }
 }

@@ -199,16 +199,34 @@ __global__ void __launch_bounds__(128) k_l2l_reg(const float *__restrict__ Lp, f
     }
 #pragma unroll
     for (int d = 0; d < D; ++d) shift_axis<D, RHO, false>(a, d, (cc[d] & 1) ? 0.5f : -0.5f);
-    // add into the child's own row in 16-byte chunks (only the shifted parent row stays live)
     float4 *own = reinterpret_cast<float4 *>(Lc + c * Pp);
+    if constexpr (RHO <= 6) {
+        // all of the child's row in flight at once, then added and stored
+        float o[P];
+        load_row<D, RHO>(Lc + c * Pp, o);
 #pragma unroll
-    for (int i = 0; i < Pp / 4; ++i) {
-        float4 v = own[i];
-        if (4 * i < P) v.x += a[4 * i];
-        if (4 * i + 1 < P) v.y += a[4 * i + 1];
-        if (4 * i + 2 < P) v.z += a[4 * i + 2];
-        if (4 * i + 3 < P) v.w += a[4 * i + 3];
-        own[i] = v;
+        for (int k = 0; k < P; ++k) o[k] += a[k];
+        store_row<D, RHO>(Lc + c * Pp, o);
+    } else {
+        // orders 7-8: add in batches of eight 16-byte chunks (a second row does not fit the
+        // registers; eight loads stay in flight)
+#pragma unroll
+        for (int i0 = 0; i0 < Pp / 4; i0 += 8) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (i0 + u < Pp / 4) v[u] = own[i0 + u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                if (i >= Pp / 4) break;
+                if (4 * i < P) v[u].x += a[4 * i];
+                if (4 * i + 1 < P) v[u].y += a[4 * i + 1];
+                if (4 * i + 2 < P) v[u].z += a[4 * i + 2];
+                if (4 * i + 3 < P) v[u].w += a[4 * i + 3];
+                own[i] = v[u];
+            }
+        }
     }
 }
 

@@ -176,4 +176,19 @@ cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *
     return cudaGetLastError();
 }
 
+// New weights for an existing sort: rec[j].w = wt[perm[j]] (the points and their order kept).
+__global__ void __launch_bounds__(256) k_reweight(int64_t n, const int *__restrict__ perm,
+                                                  const float *__restrict__ wt, float4 *__restrict__ rec) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < n) rec[j].w = wt[perm[j]];
+}
+
+cudaError_t launch_reweight(const fc2t2_plan_s *pl, cudaStream_t s, const float *wt, int64_t n, SortWork &w) {
+    if (n == 0) return cudaSuccess;
+    pl->launches[FC2T2_STAGE_SORT] += 1;
+    k_reweight<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, w.perm, wt, w.rec);
+    w.held_w = wt;
+    return cudaGetLastError();
+}
+
 }  // namespace fc2t2

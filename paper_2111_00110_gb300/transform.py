@@ -106,8 +106,11 @@ class Plan:
         return y
 
     def backward(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, ybar: torch.Tensor,
-                 need_w: bool = True, need_p: bool = True):
-        """(wbar, pbar) of Sec. 4.1 for the cotangent ybar; either may be skipped (None)."""
+                 need_w: bool = True, need_p: bool = True, reuse_forward: bool = False):
+        """(wbar, pbar) of Sec. 4.1 for the cotangent ybar; either may be skipped (None).
+
+        ``reuse_forward``: the tensors are those of this plan's last forward call and unchanged
+        since (as for an autograd layer's saved inputs), so that call's sorts are reused."""
         N, M = p.shape[0], q.shape[0]
         _check_tensor(p, "p", (N, self.dim))
         _check_tensor(w, "w", (N,))
@@ -115,8 +118,8 @@ class Plan:
         _check_tensor(ybar, "ybar", (M,))
         wbar = torch.empty(N, device=p.device, dtype=torch.float32) if need_w else None
         pbar = torch.empty(N, self.dim, device=p.device, dtype=torch.float32) if need_p else None
-        capi.backward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar),
-                      _ptr(wbar), _ptr(pbar))
+        fn = capi.backward_reuse if reuse_forward else capi.backward
+        fn(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar), _ptr(wbar), _ptr(pbar))
         return wbar, pbar
 
 
@@ -150,7 +153,9 @@ class FC2T2Function(torch.autograd.Function):
         ybar = ybar.contiguous()
         wbar = pbar = qbar = None
         if need_p or need_w:
-            wbar, pbar = ctx.plan.backward(p, w, q, ybar, need_w=need_w, need_p=need_p)
+            # the saved inputs are unchanged since the forward (autograd checks their versions);
+            # the plan reuses that call's sorts if it still holds them
+            wbar, pbar = ctx.plan.backward(p, w, q, ybar, need_w=need_w, need_p=need_p, reuse_forward=True)
         if need_q:
             qbar = ctx.plan.backward_q(p, w, q, ybar)
         return pbar, wbar, qbar, None

@@ -348,3 +348,28 @@ def test_autograd_query_gradient(lib):
     qo = oracle.backward_q(d, *f64(wl.p, wl.w, wl.q, 2.0 * y.detach().cpu().numpy()))
     assert_close(Q_.grad.cpu().numpy(), qo, what="autograd qbar")
     assert rel_l2(y.detach().cpu().numpy(), yo) <= 1e-5
+
+
+# ------------------------------------------------------------------------ sort reuse
+
+def test_backward_reuse_matches_backward(lib):
+    """fc2t2_backward_reuse after a forward on the same arrays equals fc2t2_backward (to the
+    within-cell summation order of the sorts); after a forward on other arrays it falls back to
+    sorting again, and still equals it."""
+    wl = workloads.uniform(781, 3, 6000, 5000, 16, 6, 0.08)
+    other = workloads.uniform(782, 3, 6000, 5000, 16, 6, 0.08)
+    ybar = wl.ybar()
+    for m2l in ("separable", "bf16x3"):
+        plan = make_plan(3, 16, 6, wl.sigma, wl.N, wl.M, m2l=m2l)
+        P_, W_, Q_, YB = to_dev(wl.p, wl.w, wl.q, ybar)
+        P2, W2, Q2 = to_dev(other.p, other.w, other.q)
+        wb0, pb0 = plan.backward(P_, W_, Q_, YB)
+        plan.forward(P_, W_, Q_)
+        wb1, pb1 = plan.backward(P_, W_, Q_, YB, reuse_forward=True)
+        plan.forward(P2, W2, Q2)                       # the plan now holds other sorts
+        wb2, pb2 = plan.backward(P_, W_, Q_, YB, reuse_forward=True)
+        torch.cuda.synchronize()
+        plan.check()
+        for wb, pb in ((wb1, pb1), (wb2, pb2)):
+            assert rel_l2(wb.cpu().numpy(), wb0.cpu().numpy()) <= 1e-6
+            assert rel_l2(pb.cpu().numpy(), pb0.cpu().numpy()) <= 1e-6
