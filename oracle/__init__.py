@@ -13,6 +13,8 @@ Public functions (all arrays are numpy, float64 unless stated):
     Sec. 4.1: wbar = f(p; q, ybar) (the transposed transform) and
     pbar = w * grad f(p; q, ybar).
 * ``backward_q(desc, p, w, q, ybar, sel=None, ...)`` -> qbar (gradient at the queries).
+* ``partials(desc, p, w, q, sel=None, ...)`` -> (value, first partials, second partials) of the
+    forward series at the queries (the accessor of Sec. 3, "How to use the implementation?").
 * ``direct(desc, p, w, q, sel=None)`` -> exact O(NM) sum of Eq. 1.
 * ``kernel_derivs(desc, c)`` -> d^m psi(c), |m| <= order, graded order.
 * ``multi_indices(dim, order)`` -> exponents [P, dim], graded order.
@@ -97,6 +99,12 @@ def _load():
                                           P, ctypes.c_int64,
                                           P, P, ctypes.c_int]
             lib.orc_transform.restype = ctypes.c_int
+            lib.orc_transform_h.argtypes = [ctypes.POINTER(_Desc),
+                                            P, P, ctypes.c_int64, P,
+                                            P, ctypes.c_int64, P,
+                                            P, ctypes.c_int64,
+                                            P, P, P, ctypes.c_int]
+            lib.orc_transform_h.restype = ctypes.c_int
             lib.orc_direct.argtypes = [ctypes.POINTER(_Desc), P, P, ctypes.c_int64,
                                        P, ctypes.c_int64, P, ctypes.c_int64, P]
             lib.orc_direct.restype = ctypes.c_int
@@ -173,8 +181,9 @@ def bin_cells(desc: OracleDesc, x) -> np.ndarray:
 
 
 def transform(desc: OracleDesc, src, wt, tgt, sel=None, src_cell=None, tgt_cell=None,
-              want_grad: bool = False, fault: str = "none"):
-    """Series value (and gradient) at targets of the transform of (src, wt)."""
+              want_grad: bool = False, fault: str = "none", want_hess: bool = False):
+    """Series value (and gradient) at targets of the transform of (src, wt); with ``want_hess``
+    returns (value, gradient, second partials [n, dim(dim+1)/2])."""
     D = desc.dim
     src = _f64(src).reshape(-1, D)
     tgt = _f64(tgt).reshape(-1, D)
@@ -190,14 +199,17 @@ def transform(desc: OracleDesc, src, wt, tgt, sel=None, src_cell=None, tgt_cell=
     if tgt_cell is not None:
         tgt_cell = np.ascontiguousarray(tgt_cell, dtype=np.int32)
     val = np.zeros(n_sel, dtype=np.float64)
-    grad = np.zeros((n_sel, D), dtype=np.float64) if want_grad else None
+    grad = np.zeros((n_sel, D), dtype=np.float64) if (want_grad or want_hess) else None
+    hess = np.zeros((n_sel, D * (D + 1) // 2), dtype=np.float64) if want_hess else None
     cd = desc.c()
-    rc = _load().orc_transform(ctypes.byref(cd), src.ctypes.data, wt.ctypes.data, src.shape[0],
-                               _ptr(src_cell), tgt.ctypes.data, tgt.shape[0], _ptr(tgt_cell),
-                               _ptr(sel), n_sel if sel is not None else -1,
-                               val.ctypes.data, _ptr(grad), FAULTS[fault])
+    rc = _load().orc_transform_h(ctypes.byref(cd), src.ctypes.data, wt.ctypes.data, src.shape[0],
+                                 _ptr(src_cell), tgt.ctypes.data, tgt.shape[0], _ptr(tgt_cell),
+                                 _ptr(sel), n_sel if sel is not None else -1,
+                                 val.ctypes.data, _ptr(grad), _ptr(hess), FAULTS[fault])
     if rc != 0:
         raise ValueError(f"oracle transform rejected its arguments (rc={rc})")
+    if want_hess:
+        return val, grad, hess
     return (val, grad) if want_grad else val
 
 
@@ -227,6 +239,14 @@ def backward_q(desc: OracleDesc, p, w, q, ybar, sel=None, src_cell=None, tgt_cel
                         fault=fault)
     yb = ybar if sel is None else ybar[np.asarray(sel, dtype=np.int64)]
     return grad * yb[:, None]
+
+
+def partials(desc: OracleDesc, p, w, q, sel=None, src_cell=None, tgt_cell=None, fault="none"):
+    """The accessor's queries of the forward series of (p, w) at the (selected) queries (Sec. 3,
+    "How to use the implementation?"): (value [n], first partials [n, dim], second partials
+    [n, dim(dim+1)/2] for i <= k, row-major), the binning of q held fixed."""
+    return transform(desc, p, w, q, sel=sel, src_cell=src_cell, tgt_cell=tgt_cell, want_hess=True,
+                     fault=fault)
 
 
 def direct(desc: OracleDesc, p, w, q, sel=None):

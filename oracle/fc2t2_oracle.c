@@ -360,14 +360,16 @@ static int in_list(const int *s, const int *t, int D, int level, int top, int fa
  * (finest-level linear cell index per point: used for finite differences with
  * the binning held fixed).  sel[n_sel] lists the target indices to evaluate
  * (n_sel < 0: all targets, in order).  val[j] receives the series value at
- * target sel[j]; grad (if not NULL) receives its gradient, [n_sel][dim].
+ * target sel[j]; grad (if not NULL) receives its gradient, [n_sel][dim]; hess (if not
+ * NULL) its second partials d^2/dx_i dx_k for i <= k in row-major order, [n_sel][dim(dim+1)/2]
+ * (the accessor's second partials, Sec. 3, "How to use the implementation?").
  * Returns 0 on success, negative on bad arguments.
  */
-int orc_transform(const orc_desc *d,
-                  const double *src, const double *wt, int64_t n_src, const int32_t *src_cell,
-                  const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
-                  const int64_t *sel, int64_t n_sel,
-                  double *val, double *grad, int fault) {
+int orc_transform_h(const orc_desc *d,
+                    const double *src, const double *wt, int64_t n_src, const int32_t *src_cell,
+                    const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
+                    const int64_t *sel, int64_t n_sel,
+                    double *val, double *grad, double *hess, int fault) {
     int D = d->dim, n = d->grid, rho = d->order;
     if (D < 2 || D > 3 || n < 4 || (n & (n - 1)) || rho < 0 || rho > ORC_MAXRHO) return -1;
     if (!(d->hi > d->lo)) return -1;
@@ -567,12 +569,42 @@ int orc_transform(const orc_desc *d,
                 grad[j * D + i] = g;
             }
         }
+        if (hess) {
+            /* second partials d^2/dx_i dx_k, i <= k (row-major upper triangle): both exponents
+             * lowered by one (or the one exponent by two when i = k), terms that cannot be
+             * lowered vanish */
+            int pos = 0;
+            for (int i = 0; i < D; ++i)
+                for (int k2 = i; k2 < D; ++k2, ++pos) {
+                    double hsum = 0.0;
+                    for (int a = 0; a < P; ++a) {
+                        int e[ORC_MAXD], ok = 1;
+                        for (int k = 0; k < D; ++k) e[k] = ix.ex[a * D + k];
+                        e[i] -= 1;
+                        e[k2] -= 1;
+                        for (int k = 0; k < D; ++k) ok &= e[k] >= 0;
+                        if (!ok) continue;
+                        double m = 1.0;
+                        for (int k = 0; k < D; ++k) m *= pw[k][e[k]];
+                        hsum += Lc[a] * m;
+                    }
+                    hess[j * (D * (D + 1) / 2) + pos] = hsum;
+                }
+        }
     }
 
     free(tcell);
     for (int l = 0; l < nlev; ++l) { free(Mx[l]); free(Lx[l]); free(need[l]); }
     index_free(&ix);
     return 0;
+}
+
+int orc_transform(const orc_desc *d,
+                  const double *src, const double *wt, int64_t n_src, const int32_t *src_cell,
+                  const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
+                  const int64_t *sel, int64_t n_sel,
+                  double *val, double *grad, int fault) {
+    return orc_transform_h(d, src, wt, n_src, src_cell, tgt, n_tgt, tgt_cell, sel, n_sel, val, grad, NULL, fault);
 }
 
 /* Exact O(N M) sum of Eq. 1 at the selected targets (accuracy reference). */

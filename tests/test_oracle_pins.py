@@ -294,6 +294,68 @@ def test_query_gradient_vs_central_differences(dim):
             assert abs(vals[1] - qbar[m, i]) <= 2e-5 * scale
 
 
+def _accessor_reference(dim, coef, p, w, q):
+    """Value, gradient and second partials in q of sum_n w_n psi(p_n - q) for a polynomial psi,
+    from sympy's derivatives of psi: d/dq_i psi(p - q) = -psi_,i(p - q) and
+    d^2/dq_i dq_k psi(p - q) = psi_,ik(p - q)."""
+    mis = graded(dim, 2)
+    diff = (p[:, None, :] - q[None, :, :]).reshape(-1, dim)
+    der = eval_derivs("poly", dim, 2, diff, poly=tuple(coef)).reshape(p.shape[0], q.shape[0], -1)
+    unit = [tuple(1 if j == i else 0 for j in range(dim)) for i in range(dim)]
+    val = w @ der[:, :, 0]
+    grad = np.stack([-(w @ der[:, :, mis.index(unit[i])]) for i in range(dim)], axis=1)
+    hess = np.stack([w @ der[:, :, mis.index(tuple(a + b for a, b in zip(unit[i], unit[k])))]
+                     for i in range(dim) for k in range(i, dim)], axis=1)
+    return val, grad, hess
+
+
+@pytest.mark.parametrize("name", ["r2", "one_minus_r2_sq", "odd_mixed"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_accessor_partials_polynomial_exact(name, dim):
+    """For psi a polynomial of degree <= rho the local series is the field itself, so its value,
+    first and second partials (the accessor's queries) equal the closed forms; a wrong lowering
+    of an exponent, a missing 1/h, or a swapped (i, k) slot fails it."""
+    terms = {m: v for m, v in POLYS_3D[name].items() if dim == 3 or m[2] == 0}
+    deg = max(sum(m) for m in terms)
+    coef = poly_coef(terms, dim, deg)
+    d = oracle.OracleDesc(dim=dim, grid=8, order=max(deg, 4), kernel="poly", poly_coef=coef)
+    p, w, q = small_inputs(120 + dim, dim, 50, 30)
+    v, g, h = oracle.partials(d, p, w, q)
+    rv, rg, rh = _accessor_reference(dim, coef, p, w, q)
+    for a, b in ((v, rv), (g, rg), (h, rh)):
+        assert np.max(np.abs(a - b)) <= 1e-10 * max(1.0, np.abs(b).max()), name
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_second_partials_vs_central_differences(dim):
+    """Second partials of the Gaussian series at the queries against central differences of its
+    first partials (binning of q frozen)."""
+    grid, order = (16, 4) if dim == 2 else (8, 4)
+    p, w, q = small_inputs(130 + dim, dim, 30, 40)
+    d = oracle.OracleDesc(dim=dim, grid=grid, order=order, sigma=0.12)
+    pc = oracle.bin_cells(d, p)
+    qc = oracle.bin_cells(d, q)
+    _, g, h = oracle.partials(d, p, w, q, src_cell=pc, tgt_cell=qc)
+    slot, pos = {}, 0
+    for i in range(dim):
+        for k in range(i, dim):
+            slot[(i, k)] = slot[(k, i)] = pos
+            pos += 1
+    rng = np.random.default_rng(13)
+    scale = np.abs(h).max()
+    for m in rng.choice(q.shape[0], size=6, replace=False):
+        for k in range(dim):
+            for eps, tol in ((1e-3, 2e-3), (1e-4, 2e-5)):
+                qp, qm = q.copy(), q.copy()
+                qp[m, k] += eps
+                qm[m, k] -= eps
+                gp = oracle.partials(d, p, w, qp, sel=[m], src_cell=pc, tgt_cell=qc)[1][0]
+                gm = oracle.partials(d, p, w, qm, sel=[m], src_cell=pc, tgt_cell=qc)[1][0]
+                fd = (gp - gm) / (2 * eps)
+                for i in range(dim):
+                    assert abs(fd[i] - h[m, slot[(i, k)]]) <= tol * scale, (m, i, k, eps)
+
+
 def test_truncation_error_decays_with_order():
     wl = workloads.uniform2d()
     p = wl.p.astype(np.float64)
