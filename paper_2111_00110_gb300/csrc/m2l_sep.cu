@@ -118,30 +118,97 @@ __device__ __forceinline__ void sep_task_x(const float *in0, int tl, int par, in
 }
 
 // pass Y: adds sum_{oy in SET} sum_{by <= e'} dt_oy(ky+by) T1[t+oy](kx, by, bz, e'-by) into
-// acc(ky, e')
-template <int RHO, int R, int SET>
+// acc(ky, e').  The Gaussian's derivatives are even or odd, dt_{-o}(j) = (-1)^j dt_o(j), so the
+// offsets +-o of the set are taken together: with S = T1[t+o] + T1[t-o] and A = T1[t+o] - T1[t-o]
+// (the excluded offset of the parity window contributing zero) the pair adds dt_o(j) S for even
+// j and dt_o(j) A for odd j -- one multiply-add per term for both offsets.  The paired form is
+// used at the finest level; above it the two chains' extra registers spill, and the offsets are
+// taken one at a time.
+template <int RHO, int R>
+__device__ __forceinline__ void sep_accum_y_term(float (&acc)[tri_count(R)], const float (&tri)[tri_count(R)],
+                                                 const float *dto) {
+    float dr[R + 1];
+#pragma unroll
+    for (int j = 0; j <= R; ++j) dr[j] = dto[j];
+#pragma unroll
+    for (int ky = 0; ky <= R; ++ky)
+#pragma unroll
+        for (int ep = 0; ky + ep <= R; ++ep) {
+            float sacc = acc[tri_idx(R, ky, ep)];
+#pragma unroll
+            for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
+            acc[tri_idx(R, ky, ep)] = sacc;
+        }
+}
+
+template <int RHO, int R>
+__device__ __forceinline__ void sep_accum_y_pair(float (&acc)[tri_count(R)], const float (&sum)[tri_count(R)],
+                                                 const float (&dif)[tri_count(R)], const float *dto) {
+    float dr[R + 1];
+#pragma unroll
+    for (int j = 0; j <= R; ++j) dr[j] = dto[j];
+#pragma unroll
+    for (int ky = 0; ky <= R; ++ky)
+#pragma unroll
+        for (int ep = 0; ky + ep <= R; ++ep) {
+            float sacc = acc[tri_idx(R, ky, ep)];
+#pragma unroll
+            for (int by = 0; by <= ep; ++by)
+                sacc = fmaf(dr[ky + by], ((ky + by) & 1) ? dif[tri_idx(R, by, ep - by)] : sum[tri_idx(R, by, ep - by)],
+                            sacc);
+            acc[tri_idx(R, ky, ep)] = sacc;
+        }
+}
+
+template <int RHO, int R, int SET, bool PAIRED>
 __device__ __forceinline__ void sep_accum_y(float (&acc)[tri_count(R)], const float *inb, int tl, int par, int gin,
                                             const float *s_dt) {
     constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
-#pragma unroll 1   // (unrolled, the budget-specialised bodies overflow the instruction cache)
-    for (int o = 0; o < 7; ++o) {
-        if (!in_set(SET, o - 3)) continue;
-        const bool ex = excluded(o - 3, par);
-        const float *row = inb + (tl + o) * PIN + gin;
-        float tri[tri_count(R)], dr[R + 1];
+    if (!PAIRED) {
+        // one offset at a time (the levels above the finest: the paired form's extra registers
+        // spill with their two chains)
+#pragma unroll 1
+        for (int o = 0; o < 7; ++o) {
+            if (!in_set(SET, o - 3)) continue;
+            const bool ex = excluded(o - 3, par);
+            const float *row = inb + (tl + o) * PIN + gin;
+            float tri[tri_count(R)], dr[R + 1];
+#pragma unroll
+            for (int i = 0; i < tri_count(R); ++i) tri[i] = row[i];
+#pragma unroll
+            for (int j = 0; j <= R; ++j) dr[j] = ex ? 0.0f : s_dt[o * (kMaxOrder + 1) + j];   // excluded: weight 0
+#pragma unroll
+            for (int ky = 0; ky <= R; ++ky)
+#pragma unroll
+                for (int ep = 0; ky + ep <= R; ++ep) {
+                    float sacc = acc[tri_idx(R, ky, ep)];
+#pragma unroll
+                    for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
+                    acc[tri_idx(R, ky, ep)] = sacc;
+                }
+        }
+        return;
+    }
+    if (in_set(SET, 0)) {
+        const float *row = inb + (tl + 3) * PIN + gin;
+        float tri[tri_count(R)];
 #pragma unroll
         for (int i = 0; i < tri_count(R); ++i) tri[i] = row[i];
+        sep_accum_y_term<RHO, R>(acc, tri, s_dt + 3 * (kMaxOrder + 1));
+    }
+#pragma unroll 1   // (unrolled, the budget-specialised bodies overflow the instruction cache)
+    for (int o = 1; o <= 3; ++o) {
+        if (!in_set(SET, o)) continue;
+        const bool exp_ = excluded(o, par), exm = excluded(-o, par);
+        const float *rp = inb + (tl + 3 + o) * PIN + gin, *rm = inb + (tl + 3 - o) * PIN + gin;
+        float sum[tri_count(R)], dif[tri_count(R)];
 #pragma unroll
-        for (int j = 0; j <= R; ++j) dr[j] = ex ? 0.0f : s_dt[o * (kMaxOrder + 1) + j];   // excluded: weight 0
-#pragma unroll
-        for (int ky = 0; ky <= R; ++ky)
-#pragma unroll
-            for (int ep = 0; ky + ep <= R; ++ep) {
-                float sacc = acc[tri_idx(R, ky, ep)];
-#pragma unroll
-                for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
-                acc[tri_idx(R, ky, ep)] = sacc;
-            }
+        for (int i = 0; i < tri_count(R); ++i) {
+            const float vp = exp_ ? 0.0f : rp[i], vm = exm ? 0.0f : rm[i];
+            sum[i] = vp + vm;
+            dif[i] = vp - vm;
+        }
+        sep_accum_y_pair<RHO, R>(acc, sum, dif, s_dt + (3 + o) * (kMaxOrder + 1));
     }
 }
 
@@ -174,10 +241,10 @@ __device__ __forceinline__ void sep_task_y(const float *in0, const float *in1, i
 #pragma unroll
     for (int i = 0; i < tri_count(R); ++i) acc[i] = 0.0f;
     if (chain == 0) {
-        sep_accum_y<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
-        if (!FINEST) sep_accum_y<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
+        sep_accum_y<RHO, R, kSetW, FINEST>(acc, in0, tl, par, gin, s_dt);
+        if (!FINEST) sep_accum_y<RHO, R, kSetWH, false>(acc, in1, tl, par, gin, s_dt);
     } else {
-        sep_accum_y<RHO, R, kSetH>(acc, in1, tl, par, gin, s_dt);
+        sep_accum_y<RHO, R, kSetH, false>(acc, in1, tl, par, gin, s_dt);
     }
     sep_store_y<RHO, R>(acc, out, kx, bz, s_goff);
 }
