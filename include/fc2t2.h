@@ -13,12 +13,16 @@
  *
  * Conventions shared by every entry point:
  *  - Every array pointer is a DEVICE pointer owned by the caller, unless stated.
- *    Inputs are never modified.  Arrays are dense, row-major, float32:
- *      p    [N][dim]   source positions        w     [N]       source weights
- *      q    [M][dim]   query positions         y     [M]       transform values
- *      ybar [M]        cotangent of y          wbar  [N]       dL/dw
- *      pbar [N][dim]   dL/dp
- *    (one channel; see fc2t2_plan_desc.channels).
+ *    Inputs are never modified.  Arrays are dense, row-major, float32, with C =
+ *    fc2t2_plan_desc.channels weights per source (channel-major, as the paper's
+ *    w of shape (B, C, N), Sec. 3, "How to use the implementation?"):
+ *      p    [N][dim]   source positions        w     [C][N]    source weights
+ *      q    [M][dim]   query positions         y     [C][M]    transform values
+ *      ybar [C][M]     cotangent of y          wbar  [C][N]    dL/dw
+ *      pbar [N][dim]   dL/dp (summed over the channels)
+ *      qbar [M][dim]   dL/dq (summed over the channels)
+ *    Channel c is the transform of the weights w[c]: the channels share the
+ *    points (and their sort) and are otherwise independent.
  *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.
  *    Calls are asynchronous with respect to the host: they enqueue kernels on
  *    `stream` and return.  The only host synchronisation is in fc2t2_plan_create and,
@@ -97,7 +101,7 @@ typedef struct {
     const double *poly_coef;     /* HOST pointer, n_poly coefficients; copied at plan creation */
     int n_poly;                  /* must equal C(deg + dim, dim) for some degree deg */
     double lo, hi;               /* domain [lo, hi)^dim, hi > lo */
-    int channels;                /* weights per source; this build supports 1 */
+    int channels;                /* weights per source C, 1 <= C <= 4096 */
     fc2t2_m2l_prec m2l;
     int check_domain;            /* nonzero: reject points outside the domain (synchronises) */
     int64_t max_sources;         /* workspace bound on N (>= 0) */
@@ -109,24 +113,26 @@ typedef struct {
  * Sec. 3.1), cast them to the M2L precision, and allocate the device workspace for
  * max_sources / max_queries points.  Synchronises the current device.
  * On success *out receives the plan; on failure *out is set to NULL.
+ * A plan with C > 1 channels also holds C finest-level local series for fc2t2_expand.
  * Errors: INVALID_ARG (desc or out NULL, values out of range), UNSUPPORTED
- * (channels != 1, an M2L precision this build lacks), OOM, CUDA. */
+ * (an M2L precision this build lacks for the kernel or dimension), OOM, CUDA. */
 FC2T2_API fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out);
 
 /* Release a plan and its device memory.  NULL is accepted and ignored.  The caller
  * must make sure no call on the plan is still running on the device. */
 FC2T2_API fc2t2_status fc2t2_plan_destroy(fc2t2_plan plan);
 
-/* Forward transform (Sec. 3): y[m] = sum_n psi(p[n] - q[m]) w[n] through the series.
+/* Forward transform (Sec. 3): y[c][m] = sum_n psi(p[n] - q[m]) w[c][n] through the series.
  * 0 <= N <= max_sources, 0 <= M <= max_queries; N = 0 gives y = 0.  y must not alias
- * an input.  Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
+ * an input.  The points are sorted once; each channel runs its own expansion.
+ * Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
 FC2T2_API fc2t2_status fc2t2_forward(fc2t2_plan plan, void *stream,
                            const float *p, const float *w, int64_t N,
                            const float *q, int64_t M, float *y);
 
 /* Backward pass of y = forward(p, w, q) for a cotangent ybar (Sec. 4.1):
- *   wbar[n]    = sum_m psi(q[m] - p[n]) ybar[m]             (the transposed transform)
- *   pbar[n][i] = w[n] * d/dx_i sum_m psi(x - q[m]) ybar[m] at x = p[n]
+ *   wbar[c][n] = sum_m psi(q[m] - p[n]) ybar[c][m]          (the transposed transform)
+ *   pbar[n][i] = sum_c w[c][n] * d/dx_i sum_m psi(x - q[m]) ybar[c][m] at x = p[n]
  * computed as a second transform with sources q, weights ybar and targets p, whose local
  * series is evaluated (wbar) and differentiated (pbar) at p with the binning of p held
  * fixed.  Either output may be NULL to skip it.  The kernel must be even.
@@ -140,8 +146,8 @@ FC2T2_API fc2t2_status fc2t2_backward(fc2t2_plan plan, void *stream,
  * O(N M) on the device (one thread per query, compensated FP32 summation): the sum the series
  * approximates, for measuring a plan's truncation error on a sample of queries.  Uses
  * desc->dim, desc->kernel (Gaussian only) and desc->sigma; no plan.  Device arrays as in
- * fc2t2_forward; asynchronous on `stream`.  Errors: INVALID_ARG, UNSUPPORTED (polynomial
- * kernel), CUDA. */
+ * fc2t2_forward, with desc->channels channels (w [C][N], y [C][M]); asynchronous on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED (polynomial kernel), CUDA. */
 FC2T2_API fc2t2_status fc2t2_direct(const fc2t2_plan_desc *desc, void *stream, const float *p, const float *w,
                                     int64_t N, const float *q, int64_t M, float *y);
 
@@ -165,7 +171,8 @@ FC2T2_API fc2t2_status fc2t2_backward_reuse(fc2t2_plan plan, void *stream,
                                             float *wbar, float *pbar);
 
 /* Gradient with respect to the query positions for a cotangent ybar:
- *   qbar[m][i] = ybar[m] * d/dx_i y(x) at x = q[m],   y(x) = the forward series of (p, w)
+ *   qbar[m][i] = sum_c ybar[c][m] * d/dx_i y_c(x) at x = q[m],   y_c(x) = the forward series of
+ *                (p, w[c])
  * (the derivative of the local series, the binning of q held fixed -- the same reading as pbar).
  * Sec. 4.1 derives the adjoints for p and w; the query gradient is what the paper's accessor
  * exposes as the field's first partial derivatives (Sec. 3, "How to use the implementation?"),
@@ -175,6 +182,46 @@ FC2T2_API fc2t2_status fc2t2_backward_reuse(fc2t2_plan plan, void *stream,
 FC2T2_API fc2t2_status fc2t2_backward_q(fc2t2_plan plan, void *stream,
                                         const float *p, const float *w, int64_t N,
                                         const float *q, int64_t M, const float *ybar, float *qbar);
+
+/* ---- The accessor (Sec. 3, "How to use the implementation?"): an expansion of (p, w) kept in
+ * the plan and queried at continuous positions for the field's value, first partials and second
+ * partials, at a list of points or on the meshgrid of per-axis coordinates (the paper's `vol`). */
+
+/* What an evaluation returns per point and channel (K values):
+ *   VALUE      K = 1        y_c(x)
+ *   PARTIALS   K = dim      d y_c / dx_i, i = 0 .. dim-1
+ *   PARTIALS2  K = dim (dim + 1) / 2   d^2 y_c / dx_i dx_k for i <= k, row-major:
+ *              (00, 01, 11) in 2D, (00, 01, 02, 11, 12, 22) in 3D
+ * The partials are those of the finest-level local series of the cell that holds x (the
+ * binning rule of the conventions above), the same reading as pbar and qbar. */
+typedef enum {
+    FC2T2_EVAL_VALUE = 0,
+    FC2T2_EVAL_PARTIALS = 1,
+    FC2T2_EVAL_PARTIALS2 = 2
+} fc2t2_eval;
+
+/* Expand sources (p, w) (w [C][N]) into the plan: P2M, M2M, M2L and L2L of every channel (the
+ * paper's `expand`).  The expansion stays in the plan for fc2t2_evaluate / fc2t2_evaluate_grid
+ * until the next call of any transform entry point on the plan (forward, backward,
+ * backward_reuse, backward_q, expand), which replaces it.  0 <= N <= max_sources; N = 0 gives
+ * the zero field.  Errors: INVALID_ARG, DOMAIN (check_domain), CUDA. */
+FC2T2_API fc2t2_status fc2t2_expand(fc2t2_plan plan, void *stream, const float *p, const float *w, int64_t N);
+
+/* Evaluate the held expansion at M points q [M][dim]: out [C][M][K] (K from `what`).  The points
+ * are sorted by cell for locality (0 <= M <= max_queries).  Errors: INVALID_ARG (no expansion
+ * held, bad `what`, NULL array, M out of range), DOMAIN (check_domain), CUDA. */
+FC2T2_API fc2t2_status fc2t2_evaluate(fc2t2_plan plan, void *stream, const float *q, int64_t M,
+                                      fc2t2_eval what, float *out);
+
+/* Evaluate the held expansion on the meshgrid of per-axis coordinates (the paper's `vol`):
+ * axis is a HOST array of dim DEVICE pointers, axis[i] holding count[i] >= 0 coordinates
+ * (count a HOST array of dim entries); the point (x_0, .., x_{dim-1}) = (axis[0][i_0], ..)
+ * gives out[c][i_0][i_1]([i_2])[k] (last index fastest).  No point array is formed and no
+ * sort is made: consecutive outputs step along the last axis.  Coordinates outside the domain
+ * are clamped into the edge cell (check_domain is not applied here).  Errors: INVALID_ARG (no
+ * expansion held, bad `what`, NULL array, negative count), CUDA. */
+FC2T2_API fc2t2_status fc2t2_evaluate_grid(fc2t2_plan plan, void *stream, const float *const *axis,
+                                           const int64_t *count, fc2t2_eval what, float *out);
 
 /* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
  * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,

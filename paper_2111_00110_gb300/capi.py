@@ -44,7 +44,12 @@ EXPORTS = (
     "fc2t2_direct",
     "fc2t2_backward_q",
     "fc2t2_backward_reuse",
+    "fc2t2_expand",
+    "fc2t2_evaluate",
+    "fc2t2_evaluate_grid",
 )
+# what fc2t2_evaluate returns per point and channel
+EVAL = {"value": 0, "partials": 1, "partials2": 2}
 STAGES = ("sort", "p2m", "m2m", "m2l", "l2l", "l2p", "m2l_pack")
 
 
@@ -118,6 +123,9 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_direct.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
         lib.fc2t2_backward_q.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp]
         lib.fc2t2_backward_reuse.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp, vp]
+        lib.fc2t2_expand.argtypes = [vp, vp, vp, vp, i64]
+        lib.fc2t2_evaluate.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
+        lib.fc2t2_evaluate_grid.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
@@ -161,6 +169,24 @@ def backward_reuse(plan: int, stream: int, p: int, w: int, N: int, q: int, M: in
 
 def backward_q(plan: int, stream: int, p: int, w: int, N: int, q: int, M: int, ybar: int, qbar: int) -> None:
     check(load().fc2t2_backward_q(plan, stream, p, w, N, q, M, ybar, qbar))
+
+
+def expand(plan: int, stream: int, p: int, w: int, N: int) -> None:
+    """Expand (p, w) into the plan for the accessor (device pointers)."""
+    check(load().fc2t2_expand(plan, stream, p, w, N))
+
+
+def evaluate(plan: int, stream: int, q: int, M: int, what: str, out: int) -> None:
+    """Value / first / second partials of the held expansion at M points (device pointers)."""
+    check(load().fc2t2_evaluate(plan, stream, q, M, EVAL[what], out))
+
+
+def evaluate_grid(plan: int, stream: int, axes, counts, what: str, out: int) -> None:
+    """The held expansion on the meshgrid of per-axis coordinates: axes are device pointers,
+    counts their lengths (host lists, one entry per dimension)."""
+    ax = (ctypes.c_void_p * len(axes))(*[a or None for a in axes])
+    n = (ctypes.c_int64 * len(counts))(*counts)
+    check(load().fc2t2_evaluate_grid(plan, stream, ctypes.addressof(ax), ctypes.addressof(n), EVAL[what], out))
 
 
 def direct(desc: PlanDesc, stream: int, p: int, w: int, N: int, q: int, M: int, y: int) -> None:

@@ -143,7 +143,7 @@ static void destroy(fc2t2_plan_s *pl) {
     if (!pl) return;
     for (auto &pr : pl->pending) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
     for (auto e : pl->event_pool) cudaEventDestroy(e);
-    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
+    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
     cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
     cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
     cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
@@ -268,7 +268,7 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     } else {
         return set_error(FC2T2_ERR_INVALID_ARG, "unknown kernel");
     }
-    if (d->channels != 1) return set_error(FC2T2_ERR_UNSUPPORTED, "only channels == 1 is supported");
+    if (d->channels < 1 || d->channels > 4096) return set_error(FC2T2_ERR_INVALID_ARG, "channels must be in [1, 4096]");
     if (d->m2l != FC2T2_M2L_FP32 && d->m2l != FC2T2_M2L_TF32 && d->m2l != FC2T2_M2L_BF16 &&
         d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3 && d->m2l != FC2T2_M2L_SEPARABLE)
         return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
@@ -352,6 +352,17 @@ static fc2t2_status sort_points(fc2t2_plan_s *pl, cudaStream_t s, const float *x
     return FC2T2_OK;
 }
 
+// the weights of channel `wt` gathered into an existing sort
+static fc2t2_status reweight(fc2t2_plan_s *pl, cudaStream_t s, const float *wt, int64_t n, SortWork &w) {
+    StageScope scope(pl, s, FC2T2_STAGE_SORT);
+    return check_cuda(launch_reweight(pl, s, wt, n, w), "reweight");
+}
+
+static fc2t2_status clear_flags(fc2t2_plan_s *pl, cudaStream_t s) {
+    pl->expansion_held = false;
+    return check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags");
+}
+
 // P2M .. L2L: expansion of sorted sources into finest-level local coefficients d_L (level 0)
 static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src) {
     fc2t2_status st;
@@ -408,6 +419,7 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
     pl->D = desc->dim;
     pl->n = desc->grid;
     pl->rho = desc->order;
+    pl->C = desc->channels;
     pl->P = ncoef(pl->D, pl->rho);
     pl->Pp = pad4(pl->P);
     int lg = 0;
@@ -430,6 +442,11 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
 
     if ((st = dev_alloc(&pl->d_M, (size_t)pl->G_total * pl->Pp, "moments")) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = dev_alloc(&pl->d_L, (size_t)pl->G_total * pl->Pp, "locals")) != FC2T2_OK) { destroy(pl); return st; }
+    if (pl->C > 1 &&
+        (st = dev_alloc(&pl->d_hold, (size_t)pl->C * pl->lev[0].G * pl->Pp, "channel expansions")) != FC2T2_OK) {
+        destroy(pl);
+        return st;
+    }
     if ((st = dev_alloc(&pl->d_flags, 4, "flags")) != FC2T2_OK) { destroy(pl); return st; }
     const int64_t G0 = pl->lev[0].G;
     int64_t tiles = (G0 + 4095) / 4096, tmp = 16;
@@ -458,20 +475,25 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
     if (M == 0) return FC2T2_OK;
     if (!q || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
     if (N == 0) {
-        if ((st = check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y")) != FC2T2_OK) return st;
+        if ((st = check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M * C, s), "zero y")) != FC2T2_OK) return st;
         if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
         return finish_flags(pl, s);
     }
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
-    if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
-    {
+    // one expansion per channel on the shared sorts
+    for (int c = 0; c < C; ++c) {
+        if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, y, nullptr), "l2p")) != FC2T2_OK) return st;
+        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, y + (int64_t)c * M, nullptr), "l2p")) != FC2T2_OK)
+            return st;
     }
+    pl->src.held_w = w;   // the sort of (p, w); later channels re-gather their weights
     return finish_flags(pl, s);
 }
 
@@ -483,22 +505,31 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     if (N == 0 || (!wbar && !pbar)) return FC2T2_OK;
     if (!p || !w || (M > 0 && (!q || !ybar))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
     if (M == 0) {
-        if (wbar && (st = check_cuda(cudaMemsetAsync(wbar, 0, sizeof(float) * N, s), "zero wbar")) != FC2T2_OK) return st;
+        if (wbar && (st = check_cuda(cudaMemsetAsync(wbar, 0, sizeof(float) * N * C, s), "zero wbar")) != FC2T2_OK) return st;
         if (pbar && (st = check_cuda(cudaMemsetAsync(pbar, 0, sizeof(float) * N * pl->D, s), "zero pbar")) != FC2T2_OK) return st;
         if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
         return finish_flags(pl, s);
     }
     // the transposed transform: sources q with weights ybar, targets p (Sec. 4.1)
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
-    if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
-    {
+    for (int c = 0; c < C; ++c) {
+        if (c > 0) {
+            if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
+            if (pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        }
+        if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar, pbar), "l2p grad")) != FC2T2_OK) return st;
+        // pbar sums the channels' contributions w[c] * grad g_c
+        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0),
+                             "l2p grad")) != FC2T2_OK)
+            return st;
     }
+    pl->src.held_w = w;
     return finish_flags(pl, s);
 }
 
@@ -511,18 +542,21 @@ fc2t2_status fc2t2_backward_reuse(fc2t2_plan pl, void *stream, const float *p, c
                        pl->qry.held_x == q && pl->qry.held_n == M;
     if (!reuse) return fc2t2_backward(pl, stream, p, w, N, q, M, ybar, wbar, pbar);
     cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
     // the transposed transform on the existing sorts: q becomes the sources with weights ybar
-    {
-        StageScope scope(pl, s, FC2T2_STAGE_SORT);
-        if ((st = check_cuda(launch_reweight(pl, s, ybar, M, pl->qry), "reweight")) != FC2T2_OK) return st;
-    }
-    if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
-    {
+    for (int c = 0; c < C; ++c) {
+        if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
+        // (one channel: the sort of p still carries w)
+        if (C > 1 && pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar, pbar), "l2p grad")) != FC2T2_OK) return st;
+        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0),
+                             "l2p grad")) != FC2T2_OK)
+            return st;
     }
+    pl->src.held_w = w;
     return finish_flags(pl, s);
 }
 
@@ -534,8 +568,9 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
     if (M == 0) return FC2T2_OK;
     if (!q || !ybar || !qbar || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
     fc2t2_status st;
-    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
     if (N == 0) {
         if ((st = check_cuda(cudaMemsetAsync(qbar, 0, sizeof(float) * M * pl->D, s), "zero qbar")) != FC2T2_OK) return st;
         if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
@@ -543,14 +578,96 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
     }
     // the forward expansion of (p, w), its local series differentiated at q, times ybar
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
-    if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
+    for (int c = 0; c < C; ++c) {
+        if (c > 0) {
+            if ((st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+            if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
+        }
+        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, nullptr, qbar, c > 0), "l2p grad at queries")) != FC2T2_OK)
+            return st;
+    }
+    pl->src.held_w = w;
+    pl->qry.held_w = ybar;
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_expand(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (N < 0 || N > pl->src.cap) return set_error(FC2T2_ERR_INVALID_ARG, "N outside [0, max_sources]");
+    if (N > 0 && (!p || !w)) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
+    const size_t row_floats = (size_t)pl->lev[0].G * pl->Pp;   // one channel's finest locals
+    float *hold = C > 1 ? pl->d_hold : pl->d_L;
+    fc2t2_status st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
+    if (N == 0) {
+        if ((st = check_cuda(cudaMemsetAsync(hold, 0, sizeof(float) * row_floats * C, s), "zero field")) != FC2T2_OK)
+            return st;
+        pl->expansion_held = true;
+        return FC2T2_OK;
+    }
+    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    for (int c = 0; c < C; ++c) {
+        if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
+        // (one channel: the finest level of d_L is the held expansion)
+        if (C > 1 && (st = check_cuda(cudaMemcpyAsync(hold + (size_t)c * row_floats, pl->d_L, sizeof(float) * row_floats,
+                                                      cudaMemcpyDeviceToDevice, s),
+                                      "keep channel expansion")) != FC2T2_OK)
+            return st;
+    }
+    pl->src.held_w = w;
+    if ((st = finish_flags(pl, s)) != FC2T2_OK) return st;
+    pl->expansion_held = true;
+    return FC2T2_OK;
+}
+
+fc2t2_status fc2t2_evaluate(fc2t2_plan pl, void *stream, const float *q, int64_t M, fc2t2_eval what, float *out) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (what != FC2T2_EVAL_VALUE && what != FC2T2_EVAL_PARTIALS && what != FC2T2_EVAL_PARTIALS2)
+        return set_error(FC2T2_ERR_INVALID_ARG, "unknown evaluation");
+    if (!pl->expansion_held) return set_error(FC2T2_ERR_INVALID_ARG, "no expansion held (call fc2t2_expand first)");
+    if (M < 0 || M > pl->qry.cap) return set_error(FC2T2_ERR_INVALID_ARG, "M outside [0, max_queries]");
+    if (M == 0) return FC2T2_OK;
+    if (!q || !out) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    fc2t2_status st;
+    if ((st = check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
     {
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, nullptr, qbar), "l2p grad at queries")) != FC2T2_OK)
+        if ((st = check_cuda(launch_eval_sorted(pl, s, pl->qry, M, pl->C > 1 ? pl->d_hold : pl->d_L, pl->C, (int)what, out),
+                             "evaluate")) != FC2T2_OK)
             return st;
     }
     return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_evaluate_grid(fc2t2_plan pl, void *stream, const float *const *axis, const int64_t *count,
+                                 fc2t2_eval what, float *out) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (what != FC2T2_EVAL_VALUE && what != FC2T2_EVAL_PARTIALS && what != FC2T2_EVAL_PARTIALS2)
+        return set_error(FC2T2_ERR_INVALID_ARG, "unknown evaluation");
+    if (!pl->expansion_held) return set_error(FC2T2_ERR_INVALID_ARG, "no expansion held (call fc2t2_expand first)");
+    if (!axis || !count) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    int64_t total = 1;
+    for (int d = 0; d < pl->D; ++d) {
+        if (count[d] < 0) return set_error(FC2T2_ERR_INVALID_ARG, "negative axis length");
+        if (count[d] > 0 && !axis[d]) return set_error(FC2T2_ERR_INVALID_ARG, "NULL axis");
+        if (count[d] > 0 && total > ((int64_t)1 << 40) / count[d])
+            return set_error(FC2T2_ERR_INVALID_ARG, "grid of more than 2^40 points");
+        total *= count[d];
+    }
+    if (total == 0) return FC2T2_OK;
+    if (!out) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    StageScope scope(pl, s, FC2T2_STAGE_L2P);
+    return check_cuda(launch_eval_grid(pl, s, axis, count, pl->C > 1 ? pl->d_hold : pl->d_L, pl->C, (int)what, out),
+                      "evaluate on a grid");
 }
 
 fc2t2_status fc2t2_plan_check(fc2t2_plan pl, void *stream) {
@@ -638,6 +755,7 @@ fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {
     info->m2l_useful_flops = 2.0 * q * pairs_total;
     info->m2l_issued_flops = pl->sep.enabled ? pl->sep.flops : issued;
     int64_t bytes = 2 * pl->G_total * pl->Pp * (int64_t)sizeof(float);
+    if (pl->C > 1) bytes += (int64_t)pl->C * pl->lev[0].G * pl->Pp * (int64_t)sizeof(float);
     bytes += (int64_t)pl->mma_ops_bytes + pl->tc.packed_bytes + (int64_t)pl->sep.t_bytes;
     bytes += (pl->src.cap + pl->qry.cap) * (int64_t)(5 * sizeof(int) + (pl->D + 1) * sizeof(float));
     info->device_bytes = bytes;

@@ -54,12 +54,20 @@ extern "C" fc2t2_status fc2t2_direct(const fc2t2_plan_desc *desc, void *stream, 
         return set_error(FC2T2_ERR_UNSUPPORTED, "the direct sum supports the Gaussian kernel");
     if (!(desc->sigma > 0.0)) return set_error(FC2T2_ERR_INVALID_ARG, "sigma must be positive");
     if (N < 0 || M < 0) return set_error(FC2T2_ERR_INVALID_ARG, "negative size");
+    if (desc->channels < 1 || desc->channels > 4096)
+        return set_error(FC2T2_ERR_INVALID_ARG, "channels must be in [1, 4096]");
     if ((N > 0 && (!p || !w)) || (M > 0 && (!q || !y))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     if (M == 0) return FC2T2_OK;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const float inv_2s2 = (float)(1.0 / (2.0 * desc->sigma * desc->sigma));
     const unsigned blocks = (unsigned)((M + kDirectThreads - 1) / kDirectThreads);
-    if (desc->dim == 2) k_direct<2><<<blocks, kDirectThreads, 0, s>>>(p, w, N, q, M, inv_2s2, y);
-    else k_direct<3><<<blocks, kDirectThreads, 0, s>>>(p, w, N, q, M, inv_2s2, y);
-    return check_cuda(cudaGetLastError(), "direct sum");
+    for (int c = 0; c < desc->channels; ++c) {   // w [C][N] -> y [C][M]
+        const float *wc = w ? w + (int64_t)c * N : nullptr;
+        float *yc = y + (int64_t)c * M;
+        if (desc->dim == 2) k_direct<2><<<blocks, kDirectThreads, 0, s>>>(p, wc, N, q, M, inv_2s2, yc);
+        else k_direct<3><<<blocks, kDirectThreads, 0, s>>>(p, wc, N, q, M, inv_2s2, yc);
+        const fc2t2_status st = check_cuda(cudaGetLastError(), "direct sum");
+        if (st != FC2T2_OK) return st;
+    }
+    return FC2T2_OK;
 }

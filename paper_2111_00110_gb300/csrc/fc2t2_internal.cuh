@@ -60,6 +60,14 @@ __device__ __forceinline__ bool outside(float x, float lo, float scale, int n) {
     return !(t >= 0.0f && t < (float)n);
 }
 
+// u^k / k! for k = 0..RHO (the monomials of P2M and L2P)
+template <int RHO>
+__device__ __forceinline__ void power_ladder(float u, float (&pw)[RHO + 1]) {
+    pw[0] = 1.0f;
+#pragma unroll
+    for (int k = 1; k <= RHO; ++k) pw[k] = pw[k - 1] * (u * (1.0f / (float)k));
+}
+
 // One counting sort of points into finest-level cells.
 struct SortWork {
     int64_t cap = 0;
@@ -94,6 +102,9 @@ struct fc2t2_plan_s {
     // device memory
     float *d_M = nullptr;         // [G_total][Pp]
     float *d_L = nullptr;         // [G_total][Pp]
+    int C = 1;                    // channels
+    float *d_hold = nullptr;      // [C][G0][Pp] finest-level locals of every channel (C > 1)
+    bool expansion_held = false;  // fc2t2_expand's expansion is in d_L (C = 1) or d_hold
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
     float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
     float *d_pow2 = nullptr;      // [P]  2^-|a|
@@ -164,8 +175,16 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
 cudaError_t launch_m2m(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
+// val[perm[j]] = the series at point j; grad_times_w[perm[j]] = (or += with accumulate) its
+// gradient times the point's record weight
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
-                       float *val, float *grad_times_w);
+                       float *val, float *grad_times_w, bool accumulate = false);
+// the accessor: channels [C] of finest-level locals L (channel stride G0 * Pp) evaluated at the
+// sorted points of w (out [C][m][K]) or on the meshgrid of axis[0..D-1] (out [C][n0][n1]([n2])[K])
+cudaError_t launch_eval_sorted(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
+                               const float *L, int C, int what, float *out);
+cudaError_t launch_eval_grid(const fc2t2_plan_s *pl, cudaStream_t s, const float *const *axis,
+                             const int64_t *count, const float *L, int C, int what, float *out);
 cudaError_t launch_tc_pack(const fc2t2_plan_s *pl, cudaStream_t s);
 fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
 cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s);

@@ -20,13 +20,6 @@
 
 namespace fc2t2 {
 
-template <int RHO>
-__device__ __forceinline__ void power_ladder(float u, float (&pw)[RHO + 1]) {
-    pw[0] = 1.0f;
-#pragma unroll
-    for (int k = 1; k <= RHO; ++k) pw[k] = pw[k - 1] * (u * (1.0f / (float)k));
-}
-
 constexpr int kP2MThreads = 64;
 
 template <int D, int RHO>
@@ -109,7 +102,7 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float4 *__
                                                      const int *__restrict__ perm,
                                                      const float *__restrict__ L, int n, float lo, float scale,
                                                      float h, float inv_h, float *__restrict__ val,
-                                                     float *__restrict__ grad) {
+                                                     float *__restrict__ grad, int accumulate) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     const int64_t j = (int64_t)blockIdx.x * kL2PThreads + threadIdx.x;
     if (j >= m) return;
@@ -173,14 +166,22 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float4 *__
     if (val) val[i] = value;
     if (GRAD && grad) {
         const float s = r.w * inv_h;
-        grad[(int64_t)i * D] = s * g0;
-        grad[(int64_t)i * D + 1] = s * g1;
-        if (D == 3) grad[(int64_t)i * D + 2] = s * g2;
+        float *gi = grad + (int64_t)i * D;
+        // (accumulate: the channels of one call add into the same gradient, one launch at a time)
+        if (accumulate) {
+            gi[0] += s * g0;
+            gi[1] += s * g1;
+            if (D == 3) gi[2] += s * g2;
+        } else {
+            gi[0] = s * g0;
+            gi[1] = s * g1;
+            if (D == 3) gi[2] = s * g2;
+        }
     }
 }
 
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
-                       float *val, float *grad_times_w) {
+                       float *val, float *grad_times_w, bool accumulate) {
     if (m == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((m + kL2PThreads - 1) / kL2PThreads);
     const float h = (float)pl->lev[0].h, inv_h = (float)(1.0 / pl->lev[0].h);
@@ -190,13 +191,14 @@ cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     if (grad_times_w) {
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p<D_, R_, true><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, grad_times_w),
+                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, grad_times_w,
+                            accumulate ? 1 : 0),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     } else {
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p<D_, R_, false><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, nullptr),
+                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, nullptr, 0),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     }

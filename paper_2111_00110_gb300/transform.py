@@ -2,7 +2,9 @@
 
 ``Plan`` wraps one ``fc2t2_plan`` of the C ABI; ``Plan.forward`` / ``Plan.backward`` pass
 CUDA tensors' device pointers and the current stream to ``fc2t2_forward`` /
-``fc2t2_backward``.  ``FC2T2Function`` is the explicit layer of Sec. 4 as a
+``fc2t2_backward``.  With C channels the weights are (C, N) and the values (C, M); with one
+channel they may also be one-dimensional.  ``Plan.expand`` returns the accessor of Sec. 3
+("How to use the implementation?", see ``accessor``).  ``FC2T2Function`` is the explicit layer of Sec. 4 as a
 ``torch.autograd.Function``: forward computes y = f(q; p, w), backward returns
 (pbar, wbar, None) from the transposed transform (Sec. 4.1).  PyTorch only allocates memory
 and supplies streams; every arithmetic step runs in the CUDA library.
@@ -39,8 +41,9 @@ class Plan:
     def __init__(self, dim: int, grid: int, order: int, sigma: float = 0.05, *,
                  kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
                  lo: float = 0.0, hi: float = 1.0, m2l: str = "fp32", check_domain: bool = False,
-                 max_sources: int = 1 << 20, max_queries: int = 1 << 20, device=None):
-        self.dim, self.grid, self.order = dim, grid, order
+                 max_sources: int = 1 << 20, max_queries: int = 1 << 20, channels: int = 1, device=None):
+        self.dim, self.grid, self.order, self.channels = dim, grid, order, int(channels)
+        self._serial = 0   # counts the calls that replace the plan's expansion
         self.sigma, self.kernel, self.lo, self.hi, self.m2l = sigma, kernel, lo, hi, m2l
         self.max_sources, self.max_queries = int(max_sources), int(max_queries)
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
@@ -54,7 +57,7 @@ class Plan:
             d.poly_coef = self._poly.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
             d.n_poly = int(self._poly.size)
         d.lo, d.hi = float(lo), float(hi)
-        d.channels = 1
+        d.channels = self.channels
         d.m2l = capi.M2L_PREC[m2l]
         d.check_domain = 1 if check_domain else 0
         d.max_sources, d.max_queries = self.max_sources, self.max_queries
@@ -93,15 +96,33 @@ class Plan:
     def _stream(self) -> int:
         return torch.cuda.current_stream(self.device).cuda_stream
 
+    def _chan_shape(self, t: torch.Tensor, n: int):
+        """(n,) for a one-dimensional tensor of a one-channel plan, else (C, n)."""
+        if t.dim() == 1 and self.channels == 1:
+            return (n,)
+        return (self.channels, n)
+
+    def expand(self, p: torch.Tensor, w: torch.Tensor):
+        """Keep the expansion of (p, w) in the plan and return its accessor (``Expansion``)."""
+        from .accessor import Expansion
+        N = p.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", self._chan_shape(w, N))
+        self._serial += 1
+        capi.expand(self._h, self._stream(), _ptr(p), _ptr(w), N)
+        return Expansion(self, self._serial)
+
     def forward(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor,
                 out: Optional[torch.Tensor] = None) -> torch.Tensor:
-        """y[m] = sum_n psi(p[n] - q[m]) w[n] (Sec. 3, Eq. 1) through the series."""
+        """y[c, m] = sum_n psi(p[n] - q[m]) w[c, n] (Sec. 3, Eq. 1) through the series."""
         N, M = p.shape[0], q.shape[0]
         _check_tensor(p, "p", (N, self.dim))
-        _check_tensor(w, "w", (N,))
+        _check_tensor(w, "w", self._chan_shape(w, N))
         _check_tensor(q, "q", (M, self.dim))
-        y = torch.empty(M, device=q.device, dtype=torch.float32) if out is None else out
-        _check_tensor(y, "y", (M,))
+        yshape = self._chan_shape(w, M)
+        y = torch.empty(yshape, device=q.device, dtype=torch.float32) if out is None else out
+        _check_tensor(y, "y", yshape)
+        self._serial += 1
         capi.forward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(y))
         return y
 
@@ -113,24 +134,27 @@ class Plan:
         since (as for an autograd layer's saved inputs), so that call's sorts are reused."""
         N, M = p.shape[0], q.shape[0]
         _check_tensor(p, "p", (N, self.dim))
-        _check_tensor(w, "w", (N,))
+        _check_tensor(w, "w", self._chan_shape(w, N))
         _check_tensor(q, "q", (M, self.dim))
-        _check_tensor(ybar, "ybar", (M,))
-        wbar = torch.empty(N, device=p.device, dtype=torch.float32) if need_w else None
+        _check_tensor(ybar, "ybar", self._chan_shape(w, M))
+        wbar = torch.empty(self._chan_shape(w, N), device=p.device, dtype=torch.float32) if need_w else None
         pbar = torch.empty(N, self.dim, device=p.device, dtype=torch.float32) if need_p else None
+        self._serial += 1
         fn = capi.backward_reuse if reuse_forward else capi.backward
         fn(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar), _ptr(wbar), _ptr(pbar))
         return wbar, pbar
 
 
     def backward_q(self, p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, ybar: torch.Tensor) -> torch.Tensor:
-        """qbar[m] = ybar[m] * grad y(q[m]) (the derivative of the local series at the queries)."""
+        """qbar[m] = sum_c ybar[c, m] * grad y_c(q[m]) (the derivative of the local series at the
+        queries)."""
         N, M = p.shape[0], q.shape[0]
         _check_tensor(p, "p", (N, self.dim))
-        _check_tensor(w, "w", (N,))
+        _check_tensor(w, "w", self._chan_shape(w, N))
         _check_tensor(q, "q", (M, self.dim))
-        _check_tensor(ybar, "ybar", (M,))
+        _check_tensor(ybar, "ybar", self._chan_shape(w, M))
         qbar = torch.empty(M, self.dim, device=q.device, dtype=torch.float32)
+        self._serial += 1
         capi.backward_q(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar), _ptr(qbar))
         return qbar
 
@@ -168,16 +192,17 @@ def fc2t2(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, plan: Plan) -> torc
 
 def direct(p: torch.Tensor, w: torch.Tensor, q: torch.Tensor, sigma: float) -> torch.Tensor:
     """Exact y[m] = sum_n exp(-|p[n] - q[m]|^2 / (2 sigma^2)) w[n] by brute force on the device
-    (O(N M); for error measurements on query samples)."""
+    (O(N M); for error measurements on query samples).  w is (N,) or (C, N); y is (M,) or (C, M)."""
     dim = p.shape[1]
     N, M = p.shape[0], q.shape[0]
+    C = 1 if w.dim() == 1 else w.shape[0]
     _check_tensor(p, "p", (N, dim))
-    _check_tensor(w, "w", (N,))
+    _check_tensor(w, "w", (N,) if w.dim() == 1 else (C, N))
     _check_tensor(q, "q", (M, dim))
     d = capi.PlanDesc()
     d.dim, d.grid, d.order, d.kernel, d.sigma = dim, 4, 1, capi.KERNELS["gaussian"], float(sigma)
-    d.lo, d.hi, d.channels = 0.0, 1.0, 1
-    y = torch.empty(M, device=q.device, dtype=torch.float32)
+    d.lo, d.hi, d.channels = 0.0, 1.0, C
+    y = torch.empty((M,) if w.dim() == 1 else (C, M), device=q.device, dtype=torch.float32)
     capi.direct(d, torch.cuda.current_stream(q.device).cuda_stream, _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(y))
     return y
 
@@ -191,9 +216,10 @@ def forward_batched(plans: Sequence[Plan], ps, ws, qs):
     ys = []
     for i, (pl, p, w, q) in enumerate(zip(plans, ps, ws, qs)):
         _check_tensor(p, f"p[{i}]", (p.shape[0], pl.dim))
-        _check_tensor(w, f"w[{i}]", (p.shape[0],))
+        _check_tensor(w, f"w[{i}]", pl._chan_shape(w, p.shape[0]))
         _check_tensor(q, f"q[{i}]", (q.shape[0], pl.dim))
-        ys.append(torch.empty(q.shape[0], device=q.device, dtype=torch.float32))
+        ys.append(torch.empty(pl._chan_shape(w, q.shape[0]), device=q.device, dtype=torch.float32))
+        pl._serial += 1
     stream = torch.cuda.current_stream(plans[0].device).cuda_stream if n else 0
     capi.forward_batched([pl._h for pl in plans], stream, [_ptr(p) for p in ps], [_ptr(w) for w in ws],
                          [p.shape[0] for p in ps], [_ptr(q) for q in qs], [q.shape[0] for q in qs],
@@ -209,10 +235,11 @@ def backward_batched(plans: Sequence[Plan], ps, ws, qs, ybars):
     wbars, pbars = [], []
     for i, (pl, p, w, q, yb) in enumerate(zip(plans, ps, ws, qs, ybars)):
         _check_tensor(p, f"p[{i}]", (p.shape[0], pl.dim))
-        _check_tensor(w, f"w[{i}]", (p.shape[0],))
+        _check_tensor(w, f"w[{i}]", pl._chan_shape(w, p.shape[0]))
         _check_tensor(q, f"q[{i}]", (q.shape[0], pl.dim))
-        _check_tensor(yb, f"ybar[{i}]", (q.shape[0],))
-        wbars.append(torch.empty(p.shape[0], device=p.device, dtype=torch.float32))
+        _check_tensor(yb, f"ybar[{i}]", pl._chan_shape(w, q.shape[0]))
+        wbars.append(torch.empty(pl._chan_shape(w, p.shape[0]), device=p.device, dtype=torch.float32))
+        pl._serial += 1
         pbars.append(torch.empty(p.shape[0], pl.dim, device=p.device, dtype=torch.float32))
     stream = torch.cuda.current_stream(plans[0].device).cuda_stream if n else 0
     capi.backward_batched([pl._h for pl in plans], stream, [_ptr(p) for p in ps], [_ptr(w) for w in ws],

@@ -61,6 +61,24 @@ class Workload:
         rng = np.random.default_rng(self.seed + 7919 if self.ybar_seed is None else self.ybar_seed)
         return rng.standard_normal(self.M).astype(np.float32)
 
+    def channel_weights(self, C: int) -> np.ndarray:
+        """C channels of weights [C, N] (float32): channel 0 is ``w``, the others seeded N(0,1)."""
+        rng = np.random.default_rng(self.seed + 104729)
+        out = np.empty((C, self.N), dtype=np.float32)
+        out[0] = self.w
+        if C > 1:
+            out[1:] = rng.standard_normal((C - 1, self.N)).astype(np.float32)
+        return out
+
+    def channel_ybar(self, C: int) -> np.ndarray:
+        """C channels of seeded cotangents [C, M] (float32), channel 0 equal to ``ybar()``."""
+        rng = np.random.default_rng(self.seed + 130363)
+        out = np.empty((C, self.M), dtype=np.float32)
+        out[0] = self.ybar()
+        if C > 1:
+            out[1:] = rng.standard_normal((C - 1, self.M)).astype(np.float32)
+        return out
+
 
 def _f32(a):
     return np.ascontiguousarray(a, dtype=np.float32)
