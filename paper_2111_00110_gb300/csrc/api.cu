@@ -363,8 +363,29 @@ static fc2t2_status clear_flags(fc2t2_plan_s *pl, cudaStream_t s) {
     return check_cuda(cudaMemsetAsync(pl->d_flags, 0, 2 * sizeof(int), s), "clear flags");
 }
 
-// P2M .. L2L: expansion of sorted sources into finest-level local coefficients d_L (level 0)
-static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src) {
+// Whether a transform with `targets` evaluation points skips the finest level's L2L and
+// evaluates the finest level's own M2L series plus level 1's local series at the points
+// (launch_l2p_two; the same result up to rounding, as L2L is an exact re-centring).  That trades
+// the L2L pass over every finest coefficient row for one more series per target: worth it up to
+// several targets per finest cell (more at orders 7-8, whose L2L is slower per row).
+static bool l2p_two_levels(const fc2t2_plan_s *pl, int64_t targets) {
+    const int64_t per_cell = pl->rho >= 7 ? 32 : 8;
+    return pl->nlev > 1 && targets <= per_cell * pl->lev[0].G;
+}
+
+// L2P (value and/or gradient times weight) of the sorted targets w after expand()
+static fc2t2_status evaluate_targets(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m, bool two,
+                                     float *val, float *grad, bool accumulate) {
+    StageScope scope(pl, s, FC2T2_STAGE_L2P);
+    return check_cuda(two ? launch_l2p_two(pl, s, w, m, val, grad, accumulate)
+                             : launch_l2p(pl, s, w, m, val, grad, accumulate),
+                      "l2p");
+}
+
+// P2M .. M2L .. L2L: expansion of sorted sources into local coefficients: with l2l, the finest
+// level's rows of d_L hold the whole local series; without, L2L stops at level 1 and the finest
+// level's rows hold its own M2L only (for launch_l2p_two)
+static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src, bool l2l = true) {
     fc2t2_status st;
     {
         StageScope scope(pl, s, FC2T2_STAGE_P2M);
@@ -393,7 +414,7 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
                     if ((st = check_cuda(launch_m2l(pl, s, l), "m2l")) != FC2T2_OK) return st;
         }
     }
-    for (int l = pl->nlev - 2; l >= 0; --l) {
+    for (int l = pl->nlev - 2; l >= (l2l ? 0 : 1); --l) {
         StageScope scope(pl, s, FC2T2_STAGE_L2L);
         if ((st = check_cuda(launch_l2l(pl, s, l), "l2l")) != FC2T2_OK) return st;
     }
@@ -486,11 +507,11 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
     // one expansion per channel on the shared sorts
+    const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
-        StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, y + (int64_t)c * M, nullptr), "l2p")) != FC2T2_OK)
+        if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = evaluate_targets(pl, s, pl->qry, M, two, y + (int64_t)c * M, nullptr, false)) != FC2T2_OK)
             return st;
     }
     pl->src.held_w = w;   // the sort of (p, w); later channels re-gather their weights
@@ -517,16 +538,16 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
     // the transposed transform: sources q with weights ybar, targets p (Sec. 4.1)
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    const bool two = l2p_two_levels(pl, N);
     for (int c = 0; c < C; ++c) {
         if (c > 0) {
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
             if (pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
-        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = expand(pl, s, pl->qry, !two)) != FC2T2_OK) return st;
         // pbar sums the channels' contributions w[c] * grad g_c
-        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0),
-                             "l2p grad")) != FC2T2_OK)
+        if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
+            FC2T2_OK)
             return st;
     }
     pl->src.held_w = w;
@@ -546,14 +567,14 @@ fc2t2_status fc2t2_backward_reuse(fc2t2_plan pl, void *stream, const float *p, c
     fc2t2_status st;
     if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
     // the transposed transform on the existing sorts: q becomes the sources with weights ybar
+    const bool two = l2p_two_levels(pl, N);
     for (int c = 0; c < C; ++c) {
         if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         // (one channel: the sort of p still carries w)
         if (C > 1 && pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, pl->qry)) != FC2T2_OK) return st;
-        StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->src, N, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0),
-                             "l2p grad")) != FC2T2_OK)
+        if ((st = expand(pl, s, pl->qry, !two)) != FC2T2_OK) return st;
+        if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
+            FC2T2_OK)
             return st;
     }
     pl->src.held_w = w;
@@ -579,15 +600,14 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
     // the forward expansion of (p, w), its local series differentiated at q, times ybar
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
+    const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0) {
             if ((st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
-        StageScope scope(pl, s, FC2T2_STAGE_L2P);
-        if ((st = check_cuda(launch_l2p(pl, s, pl->qry, M, nullptr, qbar, c > 0), "l2p grad at queries")) != FC2T2_OK)
-            return st;
+        if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = evaluate_targets(pl, s, pl->qry, M, two, nullptr, qbar, c > 0)) != FC2T2_OK) return st;
     }
     pl->src.held_w = w;
     pl->qry.held_w = ybar;

@@ -179,6 +179,10 @@ cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level);
 // gradient times the point's record weight
 cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                        float *val, float *grad_times_w, bool accumulate = false);
+// the same without the finest level's L2L: the finest level's own M2L series plus level 1's
+// complete local series, both about the point's cells (needs two or more levels)
+cudaError_t launch_l2p_two(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
+                           float *val, float *grad_times_w, bool accumulate = false);
 // the accessor: channels [C] of finest-level locals L (channel stride G0 * Pp) evaluated at the
 // sorted points of w (out [C][m][K]) or on the meshgrid of axis[0..D-1] (out [C][n0][n1]([n2])[K])
 cudaError_t launch_eval_sorted(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,

@@ -20,9 +20,9 @@
 // values (210 at order 6), grouped by its two leading indices; each group is a triangle.
 //
 // Every pass is a line convolution: a CTA stages a segment of one grid line (up to 32 target
-// cells plus 3 source cells on each side) of its input rows in shared memory with coalesced
-// 16-byte loads, computes its outputs from shared memory, and writes the segment's output rows
-// coalesced.  The passes move far fewer bytes and flops than the dense M2L, so they are bound by
+// cells plus the source cells their windows reach: 2 on the low side, 2 on the high side) of its
+// input rows in shared memory with coalesced loads, computes its outputs from shared memory (a
+// thread per pair of targets and task), and writes the segment's output rows coalesced.  The passes move far fewer bytes and flops than the dense M2L, so they are bound by
 // HBM bandwidth; all levels of one pass run in one launch.
 #include <algorithm>
 #include <cstring>
@@ -69,10 +69,11 @@ __device__ __forceinline__ void line_geometry(int line, int n, int64_t &base, in
 }
 
 // The parity window of a target with coordinate t along the axis is [-3, 2] (t odd) or [-2, 3]
-// (t even): the seven offsets -3..3 minus one.  Every task loops over the seven offsets (a
-// compile-time loop, so membership in the hole |o| <= 1 is known statically) and zeroes the
-// input of the excluded one, so lanes of either parity run the same instructions.
-__device__ __forceinline__ bool excluded(int off, int par) { return par ? off == 3 : off == -3; }
+// (t even).  An even target t and the odd target t + 1 therefore read the same six source rows
+// t - 2 .. t + 3: at the finest level a task owns such a pair of targets, loads each of the six rows once and applies
+// it to both, with offset k - 2 for the even target and k - 3 for the odd one (k = 0..5).  So
+// no lane computes an offset outside its window, and which offsets lie in the hole |o| <= 1 is
+// known per row at compile time (or uniformly across the warp).
 
 // offset sets of a pass: the whole window, the window minus the hole, the hole
 enum { kSetW = 0, kSetWH = 1, kSetH = 2 };
@@ -80,14 +81,189 @@ __host__ __device__ constexpr bool in_set(int set, int off) {
     return set == kSetW ? true : set == kSetH ? (off >= -1 && off <= 1) : (off < -1 || off > 1);
 }
 
+// dt_o(j) of the even target (offset k - 2) and of the odd one (offset k - 3) for row k
+__device__ __forceinline__ const float *dt_even(const float *s_dt, int k) { return s_dt + (k + 1) * (kMaxOrder + 1); }
+__device__ __forceinline__ const float *dt_odd(const float *s_dt, int k) { return s_dt + k * (kMaxOrder + 1); }
+
 // Per-task bodies, specialised on the task's degree budget R = rho - i - j (the two fixed
 // indices of the task), so that every loop has exactly the trip count the budget allows.
 
-// pass X, task (t, by, bz): T1(kx, by, bz, e) for kx + e <= R as running sums over e.  At the
-// finest level every offset of the window goes to out0; above it the window minus the hole
+// pass X, task (target pair tl, tl + 1; by, bz): T1(kx, by, bz, e) for kx + e <= R as running
+// sums over e.  At the finest level the window goes to out0; above it the window minus the hole
 // goes to out0 and the hole to out1.
 template <int RHO, int R, bool FINEST>
-__device__ __forceinline__ void sep_task_x(const float *in0, int tl, int par, int by, int bz, const float *s_dt,
+__device__ __forceinline__ void sep_task_x(const float *in0, int tl, int by, int bz, const float *s_dt,
+                                           const int *s_goff, float *out0, float *out1) {
+    constexpr int PIN = odd_pitch(pad4(ncoef(3, RHO)));
+    constexpr int POUT = odd_pitch(pad4(q4count(RHO)));
+    float ae0[R + 1], ae1[R + 1], ao0[R + 1], ao1[R + 1];   // even / odd target, out0 / out1
+    int g[R + 1];
+#pragma unroll
+    for (int kx = 0; kx <= R; ++kx) {
+        ae0[kx] = ae1[kx] = ao0[kx] = ao1[kx] = 0.0f;
+        g[kx] = s_goff[kx * (RHO + 1) + bz];
+    }
+    // e outermost: the inputs Mt[t-2..t+3](e, by, bz) feed every kx <= R - e
+#pragma unroll
+    for (int e = 0; e <= R; ++e) {
+        float v[6];
+        const int col = gidx3(e, by, bz);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = in0[(tl + k) * PIN + col];
+#pragma unroll
+        for (int kx = 0; kx + e <= R; ++kx) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const float te = dt_even(s_dt, k)[kx + e] * v[k];
+                const float to = dt_odd(s_dt, k)[kx + e] * v[k];
+                if (FINEST || in_set(kSetWH, k - 2)) ae0[kx] += te;
+                else ae1[kx] += te;
+                if (FINEST || in_set(kSetWH, k - 3)) ao0[kx] += to;
+                else ao1[kx] += to;
+            }
+            const float sg = (kx & 1) ? -1.0f : 1.0f;
+            const int idx = g[kx] + tri_idx(RHO - kx - bz, by, e);
+            out0[tl * POUT + idx] = sg * ae0[kx];
+            out0[(tl + 1) * POUT + idx] = sg * ao0[kx];
+            if (!FINEST) {
+                out1[tl * POUT + idx] = sg * ae1[kx];
+                out1[(tl + 1) * POUT + idx] = sg * ao1[kx];
+            }
+        }
+    }
+}
+
+// pass Y: adds sum_{oy in SET} sum_{by <= e'} dt_oy(ky+by) T1[t+oy](kx, by, bz, e'-by) into
+// acc(ky, e') of both targets.  Each row element T1(by, f) is loaded once and feeds every
+// (ky, e' = by + f) of both accumulators.  The row loop is not unrolled (unrolled, the
+// budget-specialised bodies overflow the instruction cache); its hole tests are warp-uniform.
+template <int RHO, int R, int SET>
+__device__ __forceinline__ void sep_accum_y(float (&ae)[tri_count(R)], float (&ao)[tri_count(R)], const float *inb,
+                                            int tl, int gin, const float *s_dt) {
+    constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
+#pragma unroll 1
+    for (int k = 0; k < 6; ++k) {
+        const bool ue = in_set(SET, k - 2), uo = in_set(SET, k - 3);
+        if (!ue && !uo) continue;
+        const float *row = inb + (tl + k) * PIN + gin;
+        float de[R + 1], dd[R + 1];
+#pragma unroll
+        for (int j = 0; j <= R; ++j) {
+            de[j] = ue ? dt_even(s_dt, k)[j] : 0.0f;
+            dd[j] = uo ? dt_odd(s_dt, k)[j] : 0.0f;
+        }
+#pragma unroll
+        for (int by = 0; by <= R; ++by)
+#pragma unroll
+            for (int f = 0; by + f <= R; ++f) {
+                const float x = row[tri_idx(R, by, f)];
+#pragma unroll
+                for (int ky = 0; ky + by + f <= R; ++ky) {
+                    const int a = tri_idx(R, ky, by + f);
+                    ae[a] = fmaf(de[ky + by], x, ae[a]);
+                    ao[a] = fmaf(dd[ky + by], x, ao[a]);
+                }
+            }
+    }
+}
+
+// T2(kx, ky, bz, e') for ky + e' <= R, stored at (bz, f = R - ky - e') of group (kx, ky) so that
+// pass Z indexes it by (bz, kz)
+template <int RHO, int R>
+__device__ __forceinline__ void sep_store_y(float (&acc)[tri_count(R)], float *outb, int kx, int bz,
+                                            const int *s_goff) {
+#pragma unroll
+    for (int ky = 0; ky <= R; ++ky) {
+        const float sg = (ky & 1) ? -1.0f : 1.0f;
+        const int rg = RHO - kx - ky;
+        float *dst = outb + s_goff[kx * (RHO + 1) + ky];
+#pragma unroll
+        for (int ep = 0; ky + ep <= R; ++ep) dst[tri_idx(rg, bz, R - ky - ep)] = sg * acc[tri_idx(R, ky, ep)];
+    }
+}
+
+// pass Y, task (target pair; kx, bz), one chain.  Finest level: the window on in0.  Above it (the
+// chains are computed one after the other into the same shared-memory rows), chain 0 (U) = the
+// window on in0 plus the window minus the hole on in1, chain 1 (V) = the hole on in1.
+template <int RHO, int R, bool FINEST>
+__device__ __forceinline__ void sep_task_y(const float *in0, const float *in1, int tl, int kx, int bz,
+                                           const float *s_dt, const int *s_goff, float *out, int chain) {
+    constexpr int POUT = odd_pitch(pad4(q4count(RHO)));
+    const int gin = s_goff[kx * (RHO + 1) + bz];
+    float ae[tri_count(R)], ao[tri_count(R)];
+#pragma unroll
+    for (int i = 0; i < tri_count(R); ++i) ae[i] = ao[i] = 0.0f;
+    if (chain == 0) {
+        sep_accum_y<RHO, R, kSetW>(ae, ao, in0, tl, gin, s_dt);
+        if (!FINEST) sep_accum_y<RHO, R, kSetWH>(ae, ao, in1, tl, gin, s_dt);
+    } else {
+        sep_accum_y<RHO, R, kSetH>(ae, ao, in1, tl, gin, s_dt);
+    }
+    sep_store_y<RHO, R>(ae, out + tl * POUT, kx, bz, s_goff);
+    sep_store_y<RHO, R>(ao, out + (tl + 1) * POUT, kx, bz, s_goff);
+}
+
+// pass Z: adds sum_{oz in SET} sum_{bz} dt_oz(kz+bz) T2[t+oz](kx, ky, bz, f = kz) into acc(kz) of
+// both targets
+template <int RHO, int R, int SET>
+__device__ __forceinline__ void sep_accum_z(float (&ae)[R + 1], float (&ao)[R + 1], const float *inb, int tl, int gin,
+                                            const float *s_dt) {
+    constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const bool ue = in_set(SET, k - 2), uo = in_set(SET, k - 3);
+        if (!ue && !uo) continue;
+        const float *row = inb + (tl + k) * PIN + gin;
+#pragma unroll
+        for (int bz = 0; bz <= R; ++bz)
+#pragma unroll
+            for (int kz = 0; kz + bz <= R; ++kz) {
+                const float x = row[tri_idx(R, bz, kz)];
+                if (ue) ae[kz] = fmaf(dt_even(s_dt, k)[kz + bz], x, ae[kz]);
+                if (uo) ao[kz] = fmaf(dt_odd(s_dt, k)[kz + bz], x, ao[kz]);
+            }
+    }
+}
+
+// pass Z, task (target pair; kx, ky): Lt(kx, ky, kz) for kz <= R; the window on in0, plus the
+// window minus the hole on in1 above the finest level
+template <int RHO, int R, bool FINEST>
+__device__ __forceinline__ void sep_task_z(const float *in0, const float *in1, int tl, int kx, int ky,
+                                           const float *s_dt, const int *s_goff, float *out0) {
+    constexpr int POUT = odd_pitch(pad4(ncoef(3, RHO)));
+    const int gin = s_goff[kx * (RHO + 1) + ky];
+    float ae[R + 1], ao[R + 1];
+#pragma unroll
+    for (int i = 0; i <= R; ++i) ae[i] = ao[i] = 0.0f;
+    sep_accum_z<RHO, R, kSetW>(ae, ao, in0, tl, gin, s_dt);
+    if (!FINEST) sep_accum_z<RHO, R, kSetWH>(ae, ao, in1, tl, gin, s_dt);
+#pragma unroll
+    for (int kz = 0; kz <= R; ++kz) {
+        const float sg = (kz & 1) ? -1.0f : 1.0f;
+        out0[tl * POUT + gidx3(kx, ky, kz)] = sg * ae[kz];
+        out0[(tl + 1) * POUT + gidx3(kx, ky, kz)] = sg * ao[kz];
+    }
+}
+
+template <int RHO, int AXIS, bool FINEST, int R>
+__device__ __forceinline__ void sep_task(const float *in0, const float *in1, int tl, int2 pr, const float *s_dt,
+                                         const int *s_goff, float *out0, float *out1, int chain) {
+    if (AXIS == 0) sep_task_x<RHO, R, FINEST>(in0, tl, pr.x, pr.y, s_dt, s_goff, out0, out1);
+    else if (AXIS == 1) sep_task_y<RHO, R, FINEST>(in0, in1, tl, pr.x, pr.y, s_dt, s_goff, out0, chain);
+    else sep_task_z<RHO, R, FINEST>(in0, in1, tl, pr.x, pr.y, s_dt, s_goff, out0);
+}
+
+// ---- Levels above the finest: a task owns one target.  There the two targets of a pair would
+// use different hole rows (a third of the paired work would be zeros), so a thread works on one
+// target over the seven offsets -3..3 and zeroes the input of the one outside its window:
+// [-3, 2] for odd t, [-2, 3] for even t.  The segment is staged with three source rows on each
+// side (row o of target tl is source t + o - 3).
+__device__ __forceinline__ bool excluded(int off, int par) { return par ? off == 3 : off == -3; }
+
+// pass X, task (t, by, bz): T1(kx, by, bz, e) for kx + e <= R as running sums over e; the window
+// minus the hole goes to out0 and the hole to out1.
+template <int RHO, int R, bool FINEST>
+__device__ __forceinline__ void cell_task_x(const float *in0, int tl, int par, int by, int bz, const float *s_dt,
                                            const int *s_goff, float *out0, float *out1) {
     constexpr int PIN = odd_pitch(pad4(ncoef(3, RHO)));
     float a0[R + 1], a1[R + 1];
@@ -118,140 +294,55 @@ __device__ __forceinline__ void sep_task_x(const float *in0, int tl, int par, in
 }
 
 // pass Y: adds sum_{oy in SET} sum_{by <= e'} dt_oy(ky+by) T1[t+oy](kx, by, bz, e'-by) into
-// acc(ky, e').  The Gaussian's derivatives are even or odd, dt_{-o}(j) = (-1)^j dt_o(j), so the
-// offsets +-o of the set are taken together: with S = T1[t+o] + T1[t-o] and A = T1[t+o] - T1[t-o]
-// (the excluded offset of the parity window contributing zero) the pair adds dt_o(j) S for even
-// j and dt_o(j) A for odd j -- one multiply-add per term for both offsets.  The paired form is
-// used at the finest level; above it the two chains' extra registers spill, and the offsets are
-// taken one at a time.
-template <int RHO, int R>
-__device__ __forceinline__ void sep_accum_y_term(float (&acc)[tri_count(R)], const float (&tri)[tri_count(R)],
-                                                 const float *dto) {
-    float dr[R + 1];
-#pragma unroll
-    for (int j = 0; j <= R; ++j) dr[j] = dto[j];
-#pragma unroll
-    for (int ky = 0; ky <= R; ++ky)
-#pragma unroll
-        for (int ep = 0; ky + ep <= R; ++ep) {
-            float sacc = acc[tri_idx(R, ky, ep)];
-#pragma unroll
-            for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
-            acc[tri_idx(R, ky, ep)] = sacc;
-        }
-}
-
-template <int RHO, int R>
-__device__ __forceinline__ void sep_accum_y_pair(float (&acc)[tri_count(R)], const float (&sum)[tri_count(R)],
-                                                 const float (&dif)[tri_count(R)], const float *dto) {
-    float dr[R + 1];
-#pragma unroll
-    for (int j = 0; j <= R; ++j) dr[j] = dto[j];
-#pragma unroll
-    for (int ky = 0; ky <= R; ++ky)
-#pragma unroll
-        for (int ep = 0; ky + ep <= R; ++ep) {
-            float sacc = acc[tri_idx(R, ky, ep)];
-#pragma unroll
-            for (int by = 0; by <= ep; ++by)
-                sacc = fmaf(dr[ky + by], ((ky + by) & 1) ? dif[tri_idx(R, by, ep - by)] : sum[tri_idx(R, by, ep - by)],
-                            sacc);
-            acc[tri_idx(R, ky, ep)] = sacc;
-        }
-}
-
-template <int RHO, int R, int SET, bool PAIRED>
-__device__ __forceinline__ void sep_accum_y(float (&acc)[tri_count(R)], const float *inb, int tl, int par, int gin,
+// acc(ky, e'), one offset at a time.
+template <int RHO, int R, int SET>
+__device__ __forceinline__ void cell_accum_y(float (&acc)[tri_count(R)], const float *inb, int tl, int par, int gin,
                                             const float *s_dt) {
     constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
-    if (!PAIRED) {
-        // one offset at a time (the levels above the finest: the paired form's extra registers
-        // spill with their two chains)
 #pragma unroll 1
-        for (int o = 0; o < 7; ++o) {
-            if (!in_set(SET, o - 3)) continue;
-            const bool ex = excluded(o - 3, par);
-            const float *row = inb + (tl + o) * PIN + gin;
-            float tri[tri_count(R)], dr[R + 1];
-#pragma unroll
-            for (int i = 0; i < tri_count(R); ++i) tri[i] = row[i];
-#pragma unroll
-            for (int j = 0; j <= R; ++j) dr[j] = ex ? 0.0f : s_dt[o * (kMaxOrder + 1) + j];   // excluded: weight 0
-#pragma unroll
-            for (int ky = 0; ky <= R; ++ky)
-#pragma unroll
-                for (int ep = 0; ky + ep <= R; ++ep) {
-                    float sacc = acc[tri_idx(R, ky, ep)];
-#pragma unroll
-                    for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
-                    acc[tri_idx(R, ky, ep)] = sacc;
-                }
-        }
-        return;
-    }
-    if (in_set(SET, 0)) {
-        const float *row = inb + (tl + 3) * PIN + gin;
-        float tri[tri_count(R)];
+    for (int o = 0; o < 7; ++o) {
+        if (!in_set(SET, o - 3)) continue;
+        const bool ex = excluded(o - 3, par);
+        const float *row = inb + (tl + o) * PIN + gin;
+        float tri[tri_count(R)], dr[R + 1];
 #pragma unroll
         for (int i = 0; i < tri_count(R); ++i) tri[i] = row[i];
-        sep_accum_y_term<RHO, R>(acc, tri, s_dt + 3 * (kMaxOrder + 1));
-    }
-#pragma unroll 1   // (unrolled, the budget-specialised bodies overflow the instruction cache)
-    for (int o = 1; o <= 3; ++o) {
-        if (!in_set(SET, o)) continue;
-        const bool exp_ = excluded(o, par), exm = excluded(-o, par);
-        const float *rp = inb + (tl + 3 + o) * PIN + gin, *rm = inb + (tl + 3 - o) * PIN + gin;
-        float sum[tri_count(R)], dif[tri_count(R)];
 #pragma unroll
-        for (int i = 0; i < tri_count(R); ++i) {
-            const float vp = exp_ ? 0.0f : rp[i], vm = exm ? 0.0f : rm[i];
-            sum[i] = vp + vm;
-            dif[i] = vp - vm;
-        }
-        sep_accum_y_pair<RHO, R>(acc, sum, dif, s_dt + (3 + o) * (kMaxOrder + 1));
+        for (int j = 0; j <= R; ++j) dr[j] = ex ? 0.0f : s_dt[o * (kMaxOrder + 1) + j];   // excluded: weight 0
+#pragma unroll
+        for (int ky = 0; ky <= R; ++ky)
+#pragma unroll
+            for (int ep = 0; ky + ep <= R; ++ep) {
+                float sacc = acc[tri_idx(R, ky, ep)];
+#pragma unroll
+                for (int by = 0; by <= ep; ++by) sacc = fmaf(dr[ky + by], tri[tri_idx(R, by, ep - by)], sacc);
+                acc[tri_idx(R, ky, ep)] = sacc;
+            }
     }
 }
 
-// T2(kx, ky, bz, e') for ky + e' <= R, stored at (bz, f = R - ky - e') of group (kx, ky) so that
-// pass Z indexes it by (bz, kz)
-template <int RHO, int R>
-__device__ __forceinline__ void sep_store_y(float (&acc)[tri_count(R)], float *outb, int kx, int bz,
-                                            const int *s_goff) {
-#pragma unroll
-    for (int ky = 0; ky <= R; ++ky) {
-        const float sg = (ky & 1) ? -1.0f : 1.0f;
-        const int rg = RHO - kx - ky;
-        float *dst = outb + s_goff[kx * (RHO + 1) + ky];
-#pragma unroll
-        for (int ep = 0; ky + ep <= R; ++ep) {
-            dst[tri_idx(rg, bz, R - ky - ep)] = sg * acc[tri_idx(R, ky, ep)];
-            acc[tri_idx(R, ky, ep)] = 0.0f;
-        }
-    }
-}
-
-// pass Y, task (t, kx, bz), one chain.  Finest level: the window on in0.  Above it (the chains
-// are computed one after the other into the same shared-memory rows), chain 0 (U) = the window
-// on in0 plus the window minus the hole on in1, chain 1 (V) = the hole on in1.
+// pass Y, task (t, kx, bz), one chain (computed one after the other into the same shared-memory
+// rows): chain 0 (U) = the window on in0 plus the window minus the hole on in1, chain 1 (V) = the
+// hole on in1.
 template <int RHO, int R, bool FINEST>
-__device__ __forceinline__ void sep_task_y(const float *in0, const float *in1, int tl, int par, int kx, int bz,
+__device__ __forceinline__ void cell_task_y(const float *in0, const float *in1, int tl, int par, int kx, int bz,
                                            const float *s_dt, const int *s_goff, float *out, int chain) {
     const int gin = s_goff[kx * (RHO + 1) + bz];
     float acc[tri_count(R)];
 #pragma unroll
     for (int i = 0; i < tri_count(R); ++i) acc[i] = 0.0f;
     if (chain == 0) {
-        sep_accum_y<RHO, R, kSetW, FINEST>(acc, in0, tl, par, gin, s_dt);
-        if (!FINEST) sep_accum_y<RHO, R, kSetWH, false>(acc, in1, tl, par, gin, s_dt);
+        cell_accum_y<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
+        if (!FINEST) cell_accum_y<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
     } else {
-        sep_accum_y<RHO, R, kSetH, false>(acc, in1, tl, par, gin, s_dt);
+        cell_accum_y<RHO, R, kSetH>(acc, in1, tl, par, gin, s_dt);
     }
     sep_store_y<RHO, R>(acc, out, kx, bz, s_goff);
 }
 
 // pass Z: adds sum_{oz in SET} sum_{bz} dt_oz(kz+bz) T2[t+oz](kx, ky, bz, f = kz) into acc(kz)
 template <int RHO, int R, int SET>
-__device__ __forceinline__ void sep_accum_z(float (&acc)[R + 1], const float *inb, int tl, int par, int gin,
+__device__ __forceinline__ void cell_accum_z(float (&acc)[R + 1], const float *inb, int tl, int par, int gin,
                                             const float *s_dt) {
     constexpr int PIN = odd_pitch(pad4(q4count(RHO)));
 #pragma unroll
@@ -274,27 +365,27 @@ __device__ __forceinline__ void sep_accum_z(float (&acc)[R + 1], const float *in
     }
 }
 
-// pass Z, task (t, kx, ky): Lt(kx, ky, kz) for kz <= R; the window on in0, plus the window minus
-// the hole on in1 above the finest level
+// pass Z, task (t, kx, ky): Lt(kx, ky, kz) for kz <= R; the window on in0 plus the window minus
+// the hole on in1
 template <int RHO, int R, bool FINEST>
-__device__ __forceinline__ void sep_task_z(const float *in0, const float *in1, int tl, int par, int kx, int ky,
+__device__ __forceinline__ void cell_task_z(const float *in0, const float *in1, int tl, int par, int kx, int ky,
                                            const float *s_dt, const int *s_goff, float *out0) {
     const int gin = s_goff[kx * (RHO + 1) + ky];
     float acc[R + 1];
 #pragma unroll
     for (int i = 0; i <= R; ++i) acc[i] = 0.0f;
-    sep_accum_z<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
-    if (!FINEST) sep_accum_z<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
+    cell_accum_z<RHO, R, kSetW>(acc, in0, tl, par, gin, s_dt);
+    if (!FINEST) cell_accum_z<RHO, R, kSetWH>(acc, in1, tl, par, gin, s_dt);
 #pragma unroll
     for (int kz = 0; kz <= R; ++kz) out0[gidx3(kx, ky, kz)] = ((kz & 1) ? -1.0f : 1.0f) * acc[kz];
 }
 
 template <int RHO, int AXIS, bool FINEST, int R>
-__device__ __forceinline__ void sep_task(const float *in0, const float *in1, int tl, int par, int2 pr,
+__device__ __forceinline__ void cell_task(const float *in0, const float *in1, int tl, int par, int2 pr,
                                          const float *s_dt, const int *s_goff, float *out0, float *out1, int chain) {
-    if (AXIS == 0) sep_task_x<RHO, R, FINEST>(in0, tl, par, pr.x, pr.y, s_dt, s_goff, out0, out1);
-    else if (AXIS == 1) sep_task_y<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0, chain);
-    else sep_task_z<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0);
+    if (AXIS == 0) cell_task_x<RHO, R, FINEST>(in0, tl, par, pr.x, pr.y, s_dt, s_goff, out0, out1);
+    else if (AXIS == 1) cell_task_y<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0, chain);
+    else cell_task_z<RHO, R, FINEST>(in0, in1, tl, par, pr.x, pr.y, s_dt, s_goff, out0);
 }
 
 template <int RHO, int AXIS>
@@ -329,7 +420,9 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     line_geometry<AXIS>(line, n, base, stride);
     const int t0 = seg * lv.seg;
     const int nt = min(lv.seg, n - t0);
-    const int nin = nt + 6;
+    // sources t0 - 2 .. t0 + nt + 1 for target pairs (finest), t0 - 3 .. t0 + nt + 2 above
+    constexpr int HALO = FINEST ? 2 : 3;
+    const int nin = nt + 2 * HALO;
 
     float *in0 = sm;
     float *in1 = in0 + nin * Pt::sin;
@@ -341,8 +434,8 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     const int *s_goff = args.goff;
     const int2 *s_pair = args.pair;
 
-    // stage the input rows of sources t0 - 3 .. t0 + nt + 2 (zero outside the grid): a warp per
-    // row, lanes across the row (coalesced scalar loads, conflict-free stores into the odd-pitch
+    // stage the input rows of sources t0 - HALO .. t0 + nt + HALO - 1 (zero outside the grid): a
+    // warp per row, lanes across the row (coalesced scalar loads, conflict-free stores into the odd-pitch
     // rows), kStageRows rows per warp in flight
     {
         constexpr int W = kSepThreads / 32, CPL = (Pt::in + 31) / 32;   // columns per lane
@@ -356,7 +449,7 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
                 float buf[kStageRows][CPL];
 #pragma unroll
                 for (int u = 0; u < kStageRows; ++u) {
-                    const int srow = t0 - 3 + r0 + u;
+                    const int srow = t0 - HALO + r0 + u;
                     const bool ok = r0 + u < nin && srow >= 0 && srow < n;
                     const float *g = gsrc + (base + (int64_t)srow * stride) * Pt::in;
 #pragma unroll
@@ -380,24 +473,41 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     }
     __syncthreads();
 
+    // finest level: target pairs (2 tp, 2 tp + 1) of the segment (t0 and nt are even); a warp's
+    // lanes cover 32 / np task slots, whose pairs the table groups by budget.  Above it: one
+    // target per task, 32 / nt slots per warp.
+    const int np = FINEST ? nt >> 1 : nt;
+    const int lg_np = __ffs(np) - 1;   // np is a power of two
 #pragma unroll 1
     for (int chain = 0; chain < NCHAIN; ++chain) {
-        for (int task = threadIdx.x; task < nt * T2; task += blockDim.x) {
-            const int tl = task % nt;
-            const int2 pr = s_pair[task / nt];
-            const int par = (t0 + tl) & 1;
-            float *o0 = out0 + tl * Pt::sout, *o1 = out1 + tl * Pt::sout;
-            // the lanes of a warp share the task's pair (and so its budget) when a segment has 32 cells
-            switch (RHO - pr.x - pr.y) {
+        for (int task = threadIdx.x; task < np * T2; task += blockDim.x) {
+            const int2 pr = s_pair[task >> lg_np];
+            if constexpr (FINEST) {
+                const int tl = 2 * (task & (np - 1));
+                switch (RHO - pr.x - pr.y) {
 #define FC2T2_SEP_R(R_)                                                                                 \
     case R_:                                                                                            \
-        if constexpr (R_ <= RHO)                                                                        \
-            sep_task<RHO, AXIS, FINEST, R_>(in0, in1, tl, par, pr, s_dt, s_goff, o0, o1, chain);       \
+        if constexpr (R_ <= RHO) sep_task<RHO, AXIS, FINEST, R_>(in0, in1, tl, pr, s_dt, s_goff, out0, out1, chain); \
         break;
-                FC2T2_SEP_R(0) FC2T2_SEP_R(1) FC2T2_SEP_R(2) FC2T2_SEP_R(3) FC2T2_SEP_R(4)
-                FC2T2_SEP_R(5) FC2T2_SEP_R(6) FC2T2_SEP_R(7) FC2T2_SEP_R(8)
+                    FC2T2_SEP_R(0) FC2T2_SEP_R(1) FC2T2_SEP_R(2) FC2T2_SEP_R(3) FC2T2_SEP_R(4)
+                    FC2T2_SEP_R(5) FC2T2_SEP_R(6) FC2T2_SEP_R(7) FC2T2_SEP_R(8)
 #undef FC2T2_SEP_R
-                default: break;
+                    default: break;
+                }
+            } else {
+                const int tl = task & (np - 1);
+                const int par = (t0 + tl) & 1;
+                float *o0 = out0 + tl * Pt::sout, *o1 = out1 + tl * Pt::sout;
+                switch (RHO - pr.x - pr.y) {
+#define FC2T2_SEP_R(R_)                                                                                 \
+    case R_:                                                                                            \
+        if constexpr (R_ <= RHO) cell_task<RHO, AXIS, false, R_>(in0, in1, tl, par, pr, s_dt, s_goff, o0, o1, chain); \
+        break;
+                    FC2T2_SEP_R(0) FC2T2_SEP_R(1) FC2T2_SEP_R(2) FC2T2_SEP_R(3) FC2T2_SEP_R(4)
+                    FC2T2_SEP_R(5) FC2T2_SEP_R(6) FC2T2_SEP_R(7) FC2T2_SEP_R(8)
+#undef FC2T2_SEP_R
+                    default: break;
+                }
             }
         }
         __syncthreads();
@@ -436,7 +546,7 @@ namespace {
 
 // shared memory of one CTA of a pass for `seg` target cells
 size_t sep_smem(int axis, int seg, bool finest, int in_pitch, int out_pitch) {
-    const int nin = seg + 6;
+    const int nin = seg + (finest ? 4 : 6);
     // two input chains above the finest level (passes Y, Z); two output rows per cell only for
     // pass X (pass Y computes its two chains one after the other into the same rows)
     const bool two = !finest && axis > 0, two_out = !finest && axis == 0;
@@ -533,13 +643,14 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
                     if (x < i0 || (x == i0 && y < i1)) off += tri_count(rho - x - y);
             a.goff[i0 * (rho + 1) + i1] = off;
         }
-    // with segments of nt < 32 cells a warp's lanes cover G = 32 / nt consecutive task slots:
-    // consecutive pairs of the cost order (mostly of equal budget) go to the same warp, so its
-    // lane groups run the same specialised body
+    // a task owns two targets at the finest level and one above it, so with segments of nt cells
+    // a warp's lanes cover G = 64 / nt or 32 / nt consecutive task slots: consecutive pairs of the
+    // cost order (mostly of equal budget) go to the same warp, so its lane groups run the same
+    // specialised body
     const int T2 = tri_count(rho);
     constexpr int W = kSepThreads / 32;
-    const int seg = pl->sep.seg[l_begin];
-    const int G = seg >= 32 ? 1 : 32 / seg;
+    const int seg = std::min(pl->sep.seg[l_begin], pl->lev[l_begin].n);
+    const int G = std::max(1, (l_begin == 0 ? 64 : 32) / seg);
     std::vector<int> used(T2, 0);
     int k = 0;
     for (int d = 0; d <= rho; ++d)

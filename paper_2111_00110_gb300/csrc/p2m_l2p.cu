@@ -9,8 +9,8 @@
 // as contiguous 16-byte stores.  Per source the work is the D power ladders plus one FMA
 // per coefficient (Sec. 3.3 counts 2 FLOPs per coefficient for P2M).
 //
-// L2P: one thread per sorted query loads its cell's coefficient row with 16-byte loads
-// (queries of one cell are adjacent, so a warp touches few rows) and evaluates
+// L2P: a CTA stages the coefficient rows of a segment of finest cells in shared memory, then
+// one thread per sorted query of those cells evaluates
 //        y = sum_k Lt(k) u^k / k!
 // as nested sums over the exponents (a Horner-like factoring).  The gradient variant also
 // returns grad y = (1/h) sum_k Lt(k + e_i) u^k / k!, times the point's weight (pbar of
@@ -97,40 +97,13 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
 
 constexpr int kL2PThreads = 128;
 
+// The series of one coefficient row at u (power ladders pw): value, and with GRAD the three
+// sums of the shifted rows sum_k Lt(k + e_i) u^k / k! (the gradient in u), nested over the
+// exponents; the results are added to value, g[].
 template <int D, int RHO, bool GRAD>
-__global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float4 *__restrict__ rec,
-                                                     const int *__restrict__ perm,
-                                                     const float *__restrict__ L, int n, float lo, float scale,
-                                                     float h, float inv_h, float *__restrict__ val,
-                                                     float *__restrict__ grad, int accumulate) {
-    constexpr int P = ncoef(D, RHO), Pp = pad4(P);
-    const int64_t j = (int64_t)blockIdx.x * kL2PThreads + threadIdx.x;
-    if (j >= m) return;
-    const float4 r = __ldg(rec + j);
-    const float xj[3] = {r.x, r.y, r.z};
-    float pw[3][RHO + 1];
-    int c = 0;
-    {
-        // the point's cell by the binning rule of the sort (same FP32 steps, same result)
-        int cd[3];
-#pragma unroll
-        for (int d = 0; d < D; ++d) cd[d] = cell_of(xj[d], lo, scale, n);
-#pragma unroll
-        for (int d = D - 1; d >= 0; --d) c = c * n + cd[d];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const float z = lo + ((float)cd[d] + 0.5f) * h;
-            power_ladder<RHO>((xj[d] - z) * inv_h, pw[d]);
-        }
-    }
-    float Lv[Pp];
-    const float4 *Lr = reinterpret_cast<const float4 *>(L + (int64_t)c * Pp);
-#pragma unroll
-    for (int i = 0; i < Pp / 4; ++i) {
-        const float4 v = __ldg(Lr + i);
-        Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
-    }
-    float value = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+__device__ __forceinline__ void series_add(const float *Lv, const float (&pw)[3][RHO + 1], float &value,
+                                           float (&g)[3]) {
+    float val = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
 #pragma unroll
     for (int a0 = 0; a0 <= RHO; ++a0) {
         float U = 0.0f, U1 = 0.0f, U2 = 0.0f;
@@ -155,54 +128,180 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p(int64_t m, const float4 *__
                 if (D == 3) U2 = fmaf(pw[1][a1], T2, U2);
             }
         }
-        value = fmaf(pw[0][a0], U, value);
+        val = fmaf(pw[0][a0], U, val);
         if (GRAD) {
             if (a0 >= 1) g0 = fmaf(pw[0][a0 - 1], U, g0);
             g1 = fmaf(pw[0][a0], U1, g1);
             if (D == 3) g2 = fmaf(pw[0][a0], U2, g2);
         }
     }
-    const int i = perm[j];
+    value += val;
+    g[0] += g0;
+    g[1] += g1;
+    g[2] += g2;
+}
+
+// the outputs of one point: val[i] = value; grad[i] = (or += with accumulate) scale * g
+template <int D, bool GRAD>
+__device__ __forceinline__ void l2p_store(int64_t i, float value, const float (&g)[3], float scale, float *val,
+                                          float *grad, int accumulate) {
     if (val) val[i] = value;
     if (GRAD && grad) {
-        const float s = r.w * inv_h;
-        float *gi = grad + (int64_t)i * D;
+        float *gi = grad + i * D;
         // (accumulate: the channels of one call add into the same gradient, one launch at a time)
         if (accumulate) {
-            gi[0] += s * g0;
-            gi[1] += s * g1;
-            if (D == 3) gi[2] += s * g2;
+            gi[0] += scale * g[0];
+            gi[1] += scale * g[1];
+            if (D == 3) gi[2] += scale * g[2];
         } else {
-            gi[0] = s * g0;
-            gi[1] = s * g1;
-            if (D == 3) gi[2] = s * g2;
+            gi[0] = scale * g[0];
+            gi[1] = scale * g[1];
+            if (D == 3) gi[2] = scale * g[2];
         }
     }
 }
 
-cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
-                       float *val, float *grad_times_w, bool accumulate) {
+// L2P, staged: a CTA owns SC = min(32, n) consecutive finest cells of one x-line.  Their
+// coefficient rows are contiguous in memory and are copied to shared memory with coalesced
+// 16-byte loads (all in flight at once); the CTA then walks the cell-sorted points of those cells
+// (a contiguous range of the sort), each thread evaluating its point from the staged row.  So no
+// thread waits on a chain of dependent global loads (record, then row).
+//
+// TWO: the finest level's L2L has not run.  L2L is an exact re-centring of a local series of
+// total degree <= rho, so the finest-level series after L2L equals the finest level's own M2L
+// series plus level 1's complete local series (its M2L and everything L2L brought down to it),
+// each about its own cell centre:
+//     y(x) = sum_k Lt_0[c_0](k) u_0^k / k!  +  sum_k Lt_1[c_1](k) u_1^k / k!,
+// c_1 = c_0 >> 1 per dimension (the tree's parent rule), u_l = (x - z_l) / h_l.  The SC / 2 parent
+// rows of the segment are contiguous too and are staged beside the finest rows.
+constexpr int kStageCells = 32;
+
+template <int D, int RHO, bool GRAD, bool TWO>
+__global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__restrict__ rec,
+                                                            const int *__restrict__ perm,
+                                                            const int *__restrict__ start,
+                                                            const float *__restrict__ L0,
+                                                            const float *__restrict__ L1, int n, float lo,
+                                                            float scale, float h0, float inv_h0, float h1,
+                                                            float inv_h1, float *__restrict__ val,
+                                                            float *__restrict__ grad, int accumulate) {
+    constexpr int Pp = pad4(ncoef(D, RHO)), P4 = Pp / 4;
+    __shared__ float4 rows[(kStageCells + (TWO ? kStageCells / 2 : 0)) * P4];
+    const int sc = n < kStageCells ? n : kStageCells;
+    const int64_t c0 = (int64_t)blockIdx.x * sc;          // first cell (x0 = c0 mod n, a multiple of sc)
+    const int x0 = (int)(c0 % n);
+    // stage the segment's rows (and its parents' rows)
+    {
+        const float4 *src0 = reinterpret_cast<const float4 *>(L0 + c0 * Pp);
+        for (int i = threadIdx.x; i < sc * P4; i += kL2PThreads) rows[i] = __ldg(src0 + i);
+        if (TWO) {
+            const int n1 = n >> 1;
+            int64_t rest = c0 / n, p0 = 0;                 // (y, z) of the line, then the parent line
+            int64_t mul = n1;
+            for (int d = 1; d < D; ++d) {
+                p0 += (rest % n >> 1) * mul;
+                rest /= n;
+                mul *= n1;
+            }
+            p0 += x0 >> 1;
+            const float4 *src1 = reinterpret_cast<const float4 *>(L1 + p0 * Pp);
+            for (int i = threadIdx.x; i < (sc >> 1) * P4; i += kL2PThreads) rows[sc * P4 + i] = __ldg(src1 + i);
+        }
+    }
+    __syncthreads();
+    const int j0 = __ldg(start + c0), j1 = __ldg(start + c0 + sc);
+    for (int j = j0 + threadIdx.x; j < j1; j += kL2PThreads) {
+        const float4 r = __ldg(rec + j);
+        const float xj[3] = {r.x, r.y, r.z};
+        int cd[3];
+#pragma unroll
+        for (int d = 0; d < D; ++d) cd[d] = cell_of(xj[d], lo, scale, n);   // the sort's binning rule
+        // the point's cell is in the segment (the sort used the same rule); clamped all the same
+        int lx = cd[0] - x0;
+        lx = lx < 0 ? 0 : (lx >= sc ? sc - 1 : lx);
+        float value = 0.0f, g[3] = {0.0f, 0.0f, 0.0f};
+        {
+            float pw[3][RHO + 1];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float z = lo + ((float)cd[d] + 0.5f) * h0;
+                power_ladder<RHO>((xj[d] - z) * inv_h0, pw[d]);
+            }
+            float Lv[Pp];
+#pragma unroll
+            for (int i = 0; i < P4; ++i) {
+                const float4 v = rows[lx * P4 + i];
+                Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
+            }
+            series_add<D, RHO, GRAD>(Lv, pw, value, g);
+        }
+        float scale_g = r.w * inv_h0;
+        if (TWO) {
+            float pw[3][RHO + 1];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const float z = lo + ((float)(cd[d] >> 1) + 0.5f) * h1;
+                power_ladder<RHO>((xj[d] - z) * inv_h1, pw[d]);
+            }
+            float Lv[Pp];
+            const int px = lx >> 1;   // x0 is even
+#pragma unroll
+            for (int i = 0; i < P4; ++i) {
+                const float4 v = rows[(sc + px) * P4 + i];
+                Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
+            }
+            float v1 = 0.0f, g1[3] = {0.0f, 0.0f, 0.0f};
+            series_add<D, RHO, GRAD>(Lv, pw, v1, g1);
+            value += v1;
+            if (GRAD) {
+                // both gradients in x: the finest part scaled by 1/h0, level 1's by 1/h1
+#pragma unroll
+                for (int d = 0; d < 3; ++d) g[d] = fmaf(inv_h1 / inv_h0, g1[d], g[d]);
+            }
+        }
+        l2p_store<D, GRAD>(perm[j], value, g, scale_g, val, grad, accumulate);
+    }
+}
+
+template <bool TWO>
+static cudaError_t launch_l2p_staged(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
+                                     float *val, float *grad_times_w, bool accumulate) {
     if (m == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((m + kL2PThreads - 1) / kL2PThreads);
-    const float h = (float)pl->lev[0].h, inv_h = (float)(1.0 / pl->lev[0].h);
+    if (TWO && pl->nlev < 2) return cudaErrorInvalidValue;
+    const int sc = pl->n < kStageCells ? pl->n : kStageCells;
+    const unsigned blocks = (unsigned)(pl->lev[0].G / sc);
+    const float h0 = (float)pl->lev[0].h, inv_h0 = (float)(1.0 / pl->lev[0].h);
+    const float h1 = TWO ? (float)pl->lev[1].h : 1.0f, inv_h1 = TWO ? (float)(1.0 / pl->lev[1].h) : 1.0f;
     const float *L0 = pl->d_L + pl->lev[0].off * pl->Pp;
+    const float *L1 = TWO ? pl->d_L + pl->lev[1].off * pl->Pp : nullptr;
     cudaError_t err = cudaSuccess;
     pl->launches[FC2T2_STAGE_L2P] += 1;
     if (grad_times_w) {
         FC2T2_DISPATCH(pl->D, pl->rho,
-                       (k_l2p<D_, R_, true><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, grad_times_w,
-                            accumulate ? 1 : 0),
+                       (k_l2p_staged<D_, R_, true, TWO><<<blocks, kL2PThreads, 0, s>>>(
+                            w.rec, w.perm, w.start, L0, L1, pl->n, pl->lo_f, pl->scale0_f, h0, inv_h0, h1, inv_h1,
+                            val, grad_times_w, accumulate ? 1 : 0),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     } else {
         FC2T2_DISPATCH(pl->D, pl->rho,
-                       (k_l2p<D_, R_, false><<<blocks, kL2PThreads, 0, s>>>(
-                            m, w.rec, w.perm, L0, pl->n, pl->lo_f, pl->scale0_f, h, inv_h, val, nullptr, 0),
+                       (k_l2p_staged<D_, R_, false, TWO><<<blocks, kL2PThreads, 0, s>>>(
+                            w.rec, w.perm, w.start, L0, L1, pl->n, pl->lo_f, pl->scale0_f, h0, inv_h0, h1, inv_h1,
+                            val, nullptr, 0),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     }
     return err;
+}
+
+cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m, float *val,
+                       float *grad_times_w, bool accumulate) {
+    return launch_l2p_staged<false>(pl, s, w, m, val, grad_times_w, accumulate);
+}
+
+cudaError_t launch_l2p_two(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m, float *val,
+                           float *grad_times_w, bool accumulate) {
+    return launch_l2p_staged<true>(pl, s, w, m, val, grad_times_w, accumulate);
 }
 
 }  // namespace fc2t2

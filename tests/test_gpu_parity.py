@@ -373,3 +373,42 @@ def test_backward_reuse_matches_backward(lib):
         for wb, pb in ((wb1, pb1), (wb2, pb2)):
             assert rel_l2(wb.cpu().numpy(), wb0.cpu().numpy()) <= 1e-6
             assert rel_l2(pb.cpu().numpy(), pb0.cpu().numpy()) <= 1e-6
+
+
+# ----------------------------------------------- L2P with and without the finest L2L
+
+@pytest.mark.parametrize("dim,order,m2l", [(3, 4, "fp32"), (3, 6, "separable"), (2, 5, "fp32"), (3, 8, "bf16x3")])
+def test_l2p_without_finest_l2l_matches_l2l(lib, dim, order, m2l):
+    """Up to a few targets per finest cell the transform skips the finest level's L2L (an exact
+    re-centring) and evaluates the finest level's own M2L series plus level 1's local series at the
+    targets; with more it runs L2L.  The same points evaluated both ways (the first targets of a
+    larger call) agree, and both match the oracle."""
+    grid = 8 if dim == 3 else 16
+    G0 = grid ** dim
+    per_cell = 32 if order >= 7 else 8
+    few, many = G0 * per_cell // 2, G0 * per_cell + 1000       # below / above the switch
+    wl = workloads.uniform(960 + dim + order, dim, 1500, many, grid, order, 0.15)
+    plan = make_plan(dim, grid, order, wl.sigma, max(wl.N, many), many, m2l=m2l)
+    P_, W_, Q_ = to_dev(wl.p, wl.w, wl.q)
+    y_many = plan.forward(P_, W_, Q_)
+    y_few = plan.forward(P_, W_, Q_[:few].contiguous())
+    torch.cuda.synchronize()
+    plan.check()
+    assert rel_l2(y_few.cpu().numpy(), y_many[:few].cpu().numpy()) <= 1e-6
+    d = odesc(dim, grid, order, wl.sigma)
+    yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q))
+    bar = TC_BARS[m2l] if m2l in TC_BARS else (REL_L2, ELEM)
+    assert_close(y_many.cpu().numpy(), yo, rel=bar[0], elem=bar[1], what="with L2L")
+    assert_close(y_few.cpu().numpy(), yo[:few], rel=bar[0], elem=bar[1], what="from levels")
+    # backward: the targets are the sources p (few of them here, so from levels), and the query
+    # gradient at few / many queries
+    ybar = np.random.default_rng(5).standard_normal(many).astype(np.float32)
+    YB = to_dev(ybar)[0]
+    wbar, pbar = plan.backward(P_, W_, Q_, YB)
+    qb_many = plan.backward_q(P_, W_, Q_, YB)
+    qb_few = plan.backward_q(P_, W_, Q_[:few].contiguous(), YB[:few].contiguous())
+    torch.cuda.synchronize()
+    wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, ybar))
+    assert_close(wbar.cpu().numpy(), wo, rel=bar[0], elem=bar[1], what="wbar from levels")
+    assert_close(pbar.cpu().numpy(), po, rel=bar[0], elem=bar[1], what="pbar from levels")
+    assert rel_l2(qb_few.cpu().numpy(), qb_many[:few].cpu().numpy()) <= 1e-5
