@@ -43,7 +43,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) of one transform's M2L launches, from an ncu capture of the current
 # kernel builds (profiles/k_m2l_sep_uniform3d.md, profiles/k_m2l_tc_bf16x3_uniform3d.md); None
 # where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"separable": (88.1 + 12.6 + 222.4 + 63.6 + 222.4 + 63.5 + 161.8 + 4.7 + 176.4 + 16.5 + 63.3 + 1.2) * 1e6,
+M2L_TRAFFIC_BYTES = {"separable": None,
                      "bf16x3": (464.0 + 82.8) * 1e6}
 
 
@@ -263,8 +263,7 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
-    plan.profile(True)
-    plan.profile_read(reset=True)
+    plan.profile_read(reset=True)           # (kernel launches are counted with profiling off too)
     sampler = ClockSampler(dev.index) if clocks else None
     if sampler:
         sampler.start()
@@ -278,14 +277,25 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
         ends[i].record(stream)
     torch.cuda.synchronize(dev)
     out.clocks = sampler.stop() if sampler else None
-    stage_ms, launches = plan.profile_read(reset=True)
-    plan.profile(False)
+    _, launches = plan.profile_read(reset=True)
     total_ms = aggregate_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     out.ms_per_step = total_ms / nsteps
     out.value = wl.M * nsteps * world / (total_ms / 1e3)
-    out.stage_ms = {k: v / nsteps for k, v in stage_ms.items()}
     out.launches = int(sum(launches.values()))
     out.launches_per_step = {k: v / nsteps for k, v in launches.items()}
+    # per-stage device time from CUDA events around each stage, in separate untimed steps: with
+    # the events on, a call runs its stages in order on the call's stream (no second stream), so
+    # the stage times add up to a little more than the timed step
+    nprof = min(nsteps, 10)
+    plan.profile(True)
+    plan.profile_read(reset=True)
+    for _ in range(nprof):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(dev)
+    stage_ms, _ = plan.profile_read(reset=True)
+    plan.profile(False)
+    out.stage_ms = {k: v / nprof for k, v in stage_ms.items()}
     out.e2e = None
     if do_e2e:
         hp, hw, hq = (torch.from_numpy(a).pin_memory() for a in (wl.p, wl.w, wl.q))

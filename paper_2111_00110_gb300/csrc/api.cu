@@ -143,6 +143,9 @@ static void destroy(fc2t2_plan_s *pl) {
     if (!pl) return;
     for (auto &pr : pl->pending) { cudaEventDestroy(pr.a); cudaEventDestroy(pr.b); }
     for (auto e : pl->event_pool) cudaEventDestroy(e);
+    if (pl->side) cudaStreamDestroy(pl->side);
+    if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
+    if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
     cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
     cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
@@ -391,6 +394,25 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
         StageScope scope(pl, s, FC2T2_STAGE_P2M);
         if ((st = check_cuda(launch_p2m(pl, s, src, pl->d_M), "p2m")) != FC2T2_OK) return st;
     }
+    if (pl->sep.enabled && pl->side && !pl->profiling && pl->nlev > 1) {
+        // The finest level's M2L needs only the finest moments; everything above it (M2M, the
+        // coarser levels' M2L, L2L down to level 1) is a chain of small launches.  The chain runs
+        // on the plan's high-priority second stream beside the finest level's passes, joined
+        // before the finest L2L / L2P.  (Stage profiling keeps the serial order below.)
+        if ((st = check_cuda(cudaEventRecord(pl->ev_fork, s), "fork")) != FC2T2_OK) return st;
+        if ((st = check_cuda(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0), "fork")) != FC2T2_OK) return st;
+        for (int l = 0; l + 1 < pl->nlev; ++l)
+            if ((st = check_cuda(launch_m2m(pl, pl->side, l), "m2m")) != FC2T2_OK) return st;
+        if ((st = check_cuda(launch_m2l_sep(pl, pl->side, 2), "m2l (separable, coarser levels)")) != FC2T2_OK)
+            return st;
+        for (int l = pl->nlev - 2; l >= 1; --l)
+            if ((st = check_cuda(launch_l2l(pl, pl->side, l), "l2l")) != FC2T2_OK) return st;
+        if ((st = check_cuda(cudaEventRecord(pl->ev_join, pl->side), "join")) != FC2T2_OK) return st;
+        if ((st = check_cuda(launch_m2l_sep(pl, s, 1), "m2l (separable, finest level)")) != FC2T2_OK) return st;
+        if ((st = check_cuda(cudaStreamWaitEvent(s, pl->ev_join, 0), "join")) != FC2T2_OK) return st;
+        if (l2l && (st = check_cuda(launch_l2l(pl, s, 0), "l2l")) != FC2T2_OK) return st;
+        return FC2T2_OK;
+    }
     {
         StageScope scope(pl, s, FC2T2_STAGE_M2M);
         for (int l = 0; l + 1 < pl->nlev; ++l)
@@ -477,6 +499,16 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
     if ((st = alloc_sort(pl->src, desc->max_sources, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = alloc_sort(pl->qry, desc->max_queries, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = build_tables(pl)) != FC2T2_OK) { destroy(pl); return st; }
+    if (pl->sep.enabled) {
+        int lo_prio = 0, hi_prio = 0;
+        cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+        if ((st = check_cuda(cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, hi_prio), "stream")) != FC2T2_OK ||
+            (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming), "event")) != FC2T2_OK ||
+            (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming), "event")) != FC2T2_OK) {
+            destroy(pl);
+            return st;
+        }
+    }
     if ((st = check_cuda(cudaMemset(pl->d_flags, 0, 4 * sizeof(int)), "clear flags")) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = check_cuda(cudaDeviceSynchronize(), "plan build")) != FC2T2_OK) { destroy(pl); return st; }
     *out = pl;

@@ -105,6 +105,10 @@ struct fc2t2_plan_s {
     int C = 1;                    // channels
     float *d_hold = nullptr;      // [C][G0][Pp] finest-level locals of every channel (C > 1)
     bool expansion_held = false;  // fc2t2_expand's expansion is in d_L (C = 1) or d_hold
+    // separable M2L: the levels above the finest run on a second stream beside the finest level's
+    // passes (fork / join by events on the call's stream)
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
     float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
     float *d_pow2 = nullptr;      // [P]  2^-|a|
@@ -191,7 +195,8 @@ cudaError_t launch_eval_grid(const fc2t2_plan_s *pl, cudaStream_t s, const float
                              const int64_t *count, const float *L, int C, int what, float *out);
 cudaError_t launch_tc_pack(const fc2t2_plan_s *pl, cudaStream_t s);
 fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
-cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s);
+// part 0: every level; 1: the finest level; 2: the levels above it
+cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s, int part = 0);
 cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s);
 // register-resident M2M / L2L for orders <= 6 (return false when not applicable)
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);

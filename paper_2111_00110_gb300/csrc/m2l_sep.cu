@@ -48,12 +48,15 @@ struct SepLevel {
     int block0;
 };
 
+constexpr int kSepMaxSlots = 192;
+
 struct SepArgs {
     SepLevel lv[kMaxLevels];
     int nlev;
     float dt[kMaxLevels][7][kMaxOrder + 1];   // dt_o(j) of each level of the launch, o = -3..3
     int goff[(kMaxOrder + 1) * (kMaxOrder + 1)];   // offset of group (i0, i1) in a 4-indexed row
-    int2 pair[tri_count(kMaxOrder)];               // task pairs (i, j), i + j <= rho, by task slot
+    int nslot;                                     // task slots of the table (pairs plus empty slots)
+    char2 pair[kSepMaxSlots];                      // task pair (i, j), i + j <= rho, by slot; (-1, -1): none
 };
 
 // In shared memory rows are padded to an odd number of floats so that the 32 lanes of a warp,
@@ -398,7 +401,6 @@ struct SepPitch {
 template <int RHO, int AXIS, bool FINEST>
 __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const SepArgs args) {
     constexpr int P = ncoef(3, RHO);
-    constexpr int T2 = tri_count(RHO);          // (i, j) pairs with i + j <= rho
     using Pt = SepPitch<RHO, AXIS>;
     constexpr bool TWO_IN = !FINEST && AXIS > 0;
     constexpr bool TWO_OUT = !FINEST && AXIS == 0;       // pass X fills both chains at once
@@ -432,7 +434,7 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     // the level's derivative table and the group / pair tables live in the launch parameters
     const float *s_dt = &args.dt[lvl][0][0];
     const int *s_goff = args.goff;
-    const int2 *s_pair = args.pair;
+    const char2 *s_pair = args.pair;
 
     // stage the input rows of sources t0 - HALO .. t0 + nt + HALO - 1 (zero outside the grid): a
     // warp per row, lanes across the row (coalesced scalar loads, conflict-free stores into the odd-pitch
@@ -480,8 +482,9 @@ __global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const
     const int lg_np = __ffs(np) - 1;   // np is a power of two
 #pragma unroll 1
     for (int chain = 0; chain < NCHAIN; ++chain) {
-        for (int task = threadIdx.x; task < np * T2; task += blockDim.x) {
-            const int2 pr = s_pair[task >> lg_np];
+        for (int task = threadIdx.x; task < np * args.nslot; task += blockDim.x) {
+            const char2 pc = s_pair[task >> lg_np];
+            const int2 pr = make_int2(pc.x, pc.y);   // (-1, -1): an empty slot (no budget matches)
             if constexpr (FINEST) {
                 const int tl = 2 * (task & (np - 1));
                 switch (RHO - pr.x - pr.y) {
@@ -628,9 +631,8 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
 }
 
 // The launch's small tables: each level's dt_o(j); the group offsets of the 4-indexed rows; the
-// task pairs (i, j) by descending cost (ascending i + j), dealt to the kSepThreads / 32 warps
-// in a snake order (0, 1, .., W-1, W-1, .., 0, ...) so that every warp gets a similar share.
-static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_end) {
+// task pairs (i, j) by slot, dealt to the kSepThreads / 32 warps as below.
+static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_end, int axis) {
     const int rho = pl->rho;
     for (int l = l_begin; l < l_end; ++l)
         for (int o = 0; o < 7; ++o)
@@ -643,28 +645,74 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
                     if (x < i0 || (x == i0 && y < i1)) off += tri_count(rho - x - y);
             a.goff[i0 * (rho + 1) + i1] = off;
         }
-    // a task owns two targets at the finest level and one above it, so with segments of nt cells
-    // a warp's lanes cover G = 64 / nt or 32 / nt consecutive task slots: consecutive pairs of the
-    // cost order (mostly of equal budget) go to the same warp, so its lane groups run the same
-    // specialised body
-    const int T2 = tri_count(rho);
+    // A task owns two targets at the finest level and one above it, so with segments of nt cells
+    // a warp's lanes cover G = 64 / nt or 32 / nt consecutive task slots, and warp w takes the
+    // slot groups w, w + W, w + 2W, ... (W warps).  Pass Y at the finest level, whose task costs
+    // spread widest (C(R+3, 3) multiply-adds per row and target: 84 at R = 6, 1 at R = 0): the
+    // pairs are grouped G at a time by equal budget (lanes of different budgets would run one
+    // after the other), and the groups are dealt longest first to the warp with the least work
+    // so far -- the CTA's compute phase ends with its busiest warp.  Unfilled slots hold (-1, -1).
     constexpr int W = kSepThreads / 32;
     const int seg = std::min(pl->sep.seg[l_begin], pl->lev[l_begin].n);
     const int G = std::max(1, (l_begin == 0 ? 64 : 32) / seg);
-    std::vector<int> used(T2, 0);
-    int k = 0;
-    for (int d = 0; d <= rho; ++d)
-        for (int i = 0; i <= d; ++i) {
-            const int m = k / G, round = m / W, pos = m % W;
-            const int w = (round & 1) ? W - 1 - pos : pos;
-            int slot = round * G * W + G * w + k % G;
-            if (slot >= T2) {   // the partial last round: the first free slot
-                slot = 0;
-                while (used[slot]) ++slot;
+    struct Group { int cost; std::vector<int2> pairs; };
+    std::vector<Group> groups;
+    for (int R = rho; R >= 0; --R) {
+        std::vector<int2> same;
+        for (int i = 0; i <= rho - R; ++i) same.push_back(make_int2(i, rho - R - i));
+        const int c = (R + 1) * (R + 2) * (R + 3) / 6;
+        for (size_t k = 0; k < same.size(); k += G)
+            groups.push_back({c, std::vector<int2>(same.begin() + k, same.begin() + std::min(same.size(), k + G))});
+    }
+    std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) { return x.cost > y.cost; });
+    if (!(axis == 1 && l_begin == 0)) {
+        // elsewhere (passes X and Z, and the levels above the finest, where a padded table's
+        // extra rounds cost more than the balance gains): the pairs in cost order, dealt to the
+        // warps in a snake order (0, 1, .., W-1, W-1, .., 0, ...) G slots at a time
+        const int T2 = tri_count(rho);
+        std::vector<int> used(T2, 0);
+        int k = 0;
+        for (int d = 0; d <= rho; ++d)
+            for (int i = 0; i <= d; ++i) {
+                const int m = k / G, round = m / W, pos = m % W;
+                const int w = (round & 1) ? W - 1 - pos : pos;
+                int slot = round * G * W + G * w + k % G;
+                if (slot >= T2) {   // the partial last round: the first free slot
+                    slot = 0;
+                    while (used[slot]) ++slot;
+                }
+                used[slot] = 1;
+                a.pair[slot] = make_char2((char)i, (char)(d - i));
+                ++k;
             }
-            used[slot] = 1;
-            a.pair[slot] = make_int2(i, d - i);
-            ++k;
+        a.nslot = T2;
+        return;
+    }
+    std::vector<int> load(W, 0);
+    std::vector<std::vector<int>> dealt(W);
+    for (int g = 0; g < (int)groups.size(); ++g) {
+        int w = 0;
+        for (int v = 1; v < W; ++v)
+            if (load[v] < load[w] || (load[v] == load[w] && dealt[v].size() < dealt[w].size())) w = v;
+        load[w] += groups[g].cost;
+        dealt[w].push_back(g);
+    }
+    size_t rounds = 0;
+    for (int w = 0; w < W; ++w) rounds = std::max(rounds, dealt[w].size());
+    a.nslot = (int)rounds * W * G;
+    if (a.nslot > kSepMaxSlots) {   // (not reached for orders <= 8): the pairs in cost order
+        a.nslot = 0;
+        for (const Group &g : groups)
+            for (const int2 &pr : g.pairs) a.pair[a.nslot++] = make_char2((char)pr.x, (char)pr.y);
+        return;
+    }
+    for (int i = 0; i < a.nslot; ++i) a.pair[i] = make_char2(-1, -1);
+    for (size_t r = 0; r < rounds; ++r)
+        for (int w = 0; w < W; ++w) {
+            if (r >= dealt[w].size()) continue;
+            const Group &g = groups[dealt[w][r]];
+            for (size_t k = 0; k < g.pairs.size(); ++k)
+                a.pair[(r * W + w) * G + k] = make_char2((char)g.pairs[k].x, (char)g.pairs[k].y);
         }
 }
 
@@ -689,17 +737,20 @@ static cudaError_t sep_launch_axis(int axis, bool finest, const SepArgs &a, unsi
     return sep_launch<RHO, 2, false>(a, blocks, smem, s);
 }
 
-// Per pass: one launch for the finest level, one for all levels above it.
-cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s) {
+// Per pass: one launch for the finest level, one for all levels above it.  `part` selects the
+// finest level's three launches (1), the levels above (2) or both (0): the two parts read and
+// write disjoint buffers and may run on different streams.
+cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s, int part) {
     const int Q4p = pl->sep.q4p;
     for (int axis = 0; axis < 3; ++axis)
         for (int fin = 1; fin >= 0; --fin) {
+            if ((part == 1 && !fin) || (part == 2 && fin)) continue;
             const int l_begin = fin ? 0 : 1, l_end = fin ? 1 : pl->nlev;
             if (l_begin >= l_end) continue;
             SepArgs a;
             std::memset(&a, 0, sizeof(a));
             a.nlev = l_end - l_begin;
-            fill_tables(pl, a, l_begin, l_end);
+            fill_tables(pl, a, l_begin, l_end, axis);
             int block = 0;
             size_t smem = 0;
             for (int l = l_begin; l < l_end; ++l) {
