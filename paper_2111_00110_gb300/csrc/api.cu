@@ -146,6 +146,7 @@ static void destroy(fc2t2_plan_s *pl) {
     if (pl->side) cudaStreamDestroy(pl->side);
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
+    if (pl->ev_sorted) cudaEventDestroy(pl->ev_sorted);
     cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
     cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
     cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
@@ -345,7 +346,7 @@ static fc2t2_status sort_points(fc2t2_plan_s *pl, cudaStream_t s, const float *x
     StageScope scope(pl, s, FC2T2_STAGE_SORT);
     fc2t2_status st;
     if ((st = check_cuda(launch_bin_count(pl, s, x, n, w), "bin")) != FC2T2_OK) return st;
-    if ((st = check_cuda(launch_scan(pl, s, w.count, w.start, pl->lev[0].G), "scan")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(pl, s, w.count, w.start, pl->lev[0].G, w.scan_tmp), "scan")) != FC2T2_OK) return st;
     w.held_x = nullptr;
     w.held_n = -1;
     if ((st = check_cuda(launch_scatter(pl, s, x, wt, n, w), "scatter")) != FC2T2_OK) return st;
@@ -353,6 +354,29 @@ static fc2t2_status sort_points(fc2t2_plan_s *pl, cudaStream_t s, const float *x
     w.held_w = wt;
     w.held_n = n;
     return FC2T2_OK;
+}
+
+// Whether an expansion runs the levels above the finest on the plan's second stream (separable
+// M2L; stage profiling keeps everything on the call's stream, in order)
+static bool forks(const fc2t2_plan_s *pl) {
+    return pl->sep.enabled && pl->side && !pl->profiling && pl->nlev > 1;
+}
+
+// Sort the targets of a transform.  When the expansion forks, the sort runs on the second stream
+// (ahead of the levels above the finest): only L2P reads it, after the join.  wait_targets()
+// makes the call's stream wait for it before L2P.
+static fc2t2_status sort_targets(fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt, int64_t n,
+                                 SortWork &w) {
+    if (!forks(pl)) return sort_points(pl, s, x, wt, n, w);
+    fc2t2_status st;
+    if ((st = check_cuda(cudaEventRecord(pl->ev_fork, s), "fork")) != FC2T2_OK) return st;
+    if ((st = check_cuda(cudaStreamWaitEvent(pl->side, pl->ev_fork, 0), "fork")) != FC2T2_OK) return st;
+    if ((st = sort_points(pl, pl->side, x, wt, n, w)) != FC2T2_OK) return st;
+    return check_cuda(cudaEventRecord(pl->ev_sorted, pl->side), "join");
+}
+
+static fc2t2_status wait_targets(fc2t2_plan_s *pl, cudaStream_t s) {
+    return forks(pl) ? check_cuda(cudaStreamWaitEvent(s, pl->ev_sorted, 0), "join") : FC2T2_OK;
 }
 
 // the weights of channel `wt` gathered into an existing sort
@@ -394,7 +418,7 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src
         StageScope scope(pl, s, FC2T2_STAGE_P2M);
         if ((st = check_cuda(launch_p2m(pl, s, src, pl->d_M), "p2m")) != FC2T2_OK) return st;
     }
-    if (pl->sep.enabled && pl->side && !pl->profiling && pl->nlev > 1) {
+    if (forks(pl)) {
         // The finest level's M2L needs only the finest moments; everything above it (M2M, the
         // coarser levels' M2L, L2L down to level 1) is a chain of small launches.  The chain runs
         // on the plan's high-priority second stream beside the finest level's passes, joined
@@ -495,16 +519,19 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
     int64_t tiles = (G0 + 4095) / 4096, tmp = 16;
     while (tiles > 1) { tmp += 2 * tiles + 1; tiles = (tiles + 4095) / 4096; }
     pl->scan_tmp_len = tmp;
-    if ((st = dev_alloc(&pl->d_scan_tmp, (size_t)tmp, "scan workspace")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = dev_alloc(&pl->d_scan_tmp, 2 * (size_t)tmp, "scan workspace")) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = alloc_sort(pl->src, desc->max_sources, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = alloc_sort(pl->qry, desc->max_queries, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
+    pl->src.scan_tmp = pl->d_scan_tmp;
+    pl->qry.scan_tmp = pl->d_scan_tmp + tmp;
     if ((st = build_tables(pl)) != FC2T2_OK) { destroy(pl); return st; }
     if (pl->sep.enabled) {
         int lo_prio = 0, hi_prio = 0;
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
         if ((st = check_cuda(cudaStreamCreateWithPriority(&pl->side, cudaStreamNonBlocking, hi_prio), "stream")) != FC2T2_OK ||
             (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_fork, cudaEventDisableTiming), "event")) != FC2T2_OK ||
-            (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming), "event")) != FC2T2_OK) {
+            (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_join, cudaEventDisableTiming), "event")) != FC2T2_OK ||
+            (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_sorted, cudaEventDisableTiming), "event")) != FC2T2_OK) {
             destroy(pl);
             return st;
         }
@@ -536,13 +563,14 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
         if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;   // domain check
         return finish_flags(pl, s);
     }
+    if ((st = sort_targets(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
-    if ((st = sort_points(pl, s, q, nullptr, M, pl->qry)) != FC2T2_OK) return st;
     // one expansion per channel on the shared sorts
     const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
         if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, y + (int64_t)c * M, nullptr, false)) != FC2T2_OK)
             return st;
     }
@@ -568,8 +596,8 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
         return finish_flags(pl, s);
     }
     // the transposed transform: sources q with weights ybar, targets p (Sec. 4.1)
+    if ((st = sort_targets(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
-    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     const bool two = l2p_two_levels(pl, N);
     for (int c = 0; c < C; ++c) {
         if (c > 0) {
@@ -577,6 +605,7 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
             if (pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
         }
         if ((st = expand(pl, s, pl->qry, !two)) != FC2T2_OK) return st;
+        if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         // pbar sums the channels' contributions w[c] * grad g_c
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
             FC2T2_OK)
@@ -630,8 +659,8 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
         return finish_flags(pl, s);
     }
     // the forward expansion of (p, w), its local series differentiated at q, times ybar
+    if ((st = sort_targets(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
-    if ((st = sort_points(pl, s, q, ybar, M, pl->qry)) != FC2T2_OK) return st;
     const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0) {
@@ -639,6 +668,7 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         }
         if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, nullptr, qbar, c > 0)) != FC2T2_OK) return st;
     }
     pl->src.held_w = w;

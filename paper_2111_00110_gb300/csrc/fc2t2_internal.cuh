@@ -77,6 +77,7 @@ struct SortWork {
     int *rank = nullptr;        // [cap]  position of point i within its cell
     int *perm = nullptr;        // [cap]  sorted position -> input index
     float4 *rec = nullptr;      // [cap]  sorted point: (x0, x1, x2 or 0, weight or 0)
+    int *scan_tmp = nullptr;    // block sums of this sort's prefix scan (the two sorts may run at once)
     // what the workspace holds: the points and weights arrays (and count) it last sorted
     const float *held_x = nullptr, *held_w = nullptr;
     int64_t held_n = -1;
@@ -108,7 +109,7 @@ struct fc2t2_plan_s {
     // separable M2L: the levels above the finest run on a second stream beside the finest level's
     // passes (fork / join by events on the call's stream)
     cudaStream_t side = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sorted = nullptr;
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
     float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
     float *d_pow2 = nullptr;      // [P]  2^-|a|
@@ -171,7 +172,7 @@ fc2t2_status check_cuda(cudaError_t e, const char *what);
 // launchers (return cudaGetLastError() of the launch)
 cudaError_t launch_bin_count(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, int64_t n,
                              SortWork &w);
-cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n);
+cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n, int *tmp);
 cudaError_t launch_reweight(const fc2t2_plan_s *pl, cudaStream_t s, const float *wt, int64_t n, SortWork &w);
 cudaError_t launch_scatter(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, const float *wt,
                            int64_t n, SortWork &w);

@@ -276,7 +276,7 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
 
     // the same kernels as fc2t2_forward, on scratch-array pointers
     if ((st = check_cuda(launch_bin_count(&pl, s, p, N, pl.src), "bin")) != FC2T2_OK) return st;
-    if ((st = check_cuda(launch_scan(&pl, s, pl.src.count, pl.src.start, pl.lev[0].G), "scan")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(&pl, s, pl.src.count, pl.src.start, pl.lev[0].G, pl.d_scan_tmp), "scan")) != FC2T2_OK) return st;
     if ((st = check_cuda(launch_scatter(&pl, s, p, w, N, pl.src), "scatter")) != FC2T2_OK) return st;
     if ((st = check_cuda(launch_p2m(&pl, s, pl.src, pl.d_M), "p2m")) != FC2T2_OK) return st;
     for (int l = 0; l + 1 < pl.nlev; ++l)
@@ -286,7 +286,7 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
         if (l + 1 < pl.nlev && (st = check_cuda(launch_l2l(&pl, s, l), "l2l")) != FC2T2_OK) return st;
     }
     if ((st = check_cuda(launch_bin_count(&pl, s, q, M, pl.qry), "bin")) != FC2T2_OK) return st;
-    if ((st = check_cuda(launch_scan(&pl, s, pl.qry.count, pl.qry.start, pl.lev[0].G), "scan")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_scan(&pl, s, pl.qry.count, pl.qry.start, pl.lev[0].G, pl.d_scan_tmp), "scan")) != FC2T2_OK) return st;
     if ((st = check_cuda(launch_scatter(&pl, s, q, nullptr, M, pl.qry), "scatter")) != FC2T2_OK) return st;
     return check_cuda(launch_l2p(&pl, s, pl.qry, M, y, nullptr), "l2p");
 }

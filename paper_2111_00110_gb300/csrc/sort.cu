@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_tile(const int *__restric
 }
 
 // Exclusive scan of in[0..n) into out[0..n], out[n] = total.  Recursive reduce-then-scan;
-// the block sums of every level live in pl->d_scan_tmp.
+// the block sums of every level live in `tmp` (one workspace per sort).
 static cudaError_t scan_rec(cudaStream_t s, const int *in, int *out, int64_t n, int *tmp,
                             bool write_total, int64_t &launches) {
     int64_t tiles = (n + kScanTile - 1) / kScanTile;
@@ -144,8 +144,8 @@ static cudaError_t scan_rec(cudaStream_t s, const int *in, int *out, int64_t n, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n) {
-    return scan_rec(s, in, out, n, pl->d_scan_tmp, true, pl->launches[FC2T2_STAGE_SORT]);
+cudaError_t launch_scan(const fc2t2_plan_s *pl, cudaStream_t s, const int *in, int *out, int64_t n, int *tmp) {
+    return scan_rec(s, in, out, n, tmp, true, pl->launches[FC2T2_STAGE_SORT]);
 }
 
 // ---------------------------------------------------------------- scatter
