@@ -400,14 +400,25 @@ def stage_roofline(m: Measured, wl, peaks):
     row = 4 * Pp
     G = [(wl.grid >> l) ** 3 for l in range(m.info["levels"])]
     N, M = wl.N, wl.M
-    # per transform; the forward has sources (p, w) and targets q, the backward sources (q, ybar)
-    # and targets p (with w for pbar)
-    sort = (12 + 4 + 16 + 4) * N + (12 + 12 + 4) * M          # fwd: sort p,w; sort q
-    sort += (12 + 4 + 16 + 4) * M + (12 + 4 + 16 + 4) * N      # bwd: sort q,ybar; sort p,w
+    # per step: the forward sorts (p, w) (16 B read, a 16-byte record and a 4-byte index written
+    # per point) and q (12 B read, 20 B written); the backward reuses both sorts and gathers ybar
+    # into the record of each sorted query (index and ybar read, 4 B written)
+    sort = (16 + 20) * N + (12 + 20) * M + (4 + 4 + 4) * M
     p2m = (16 * N + row * G[0]) + (16 * M + row * G[0])
     m2m = 2 * sum(row * (G[l] + G[l + 1]) for l in range(len(G) - 1))
-    l2l = 2 * sum(row * (G[l + 1] + 2 * G[l]) for l in range(len(G) - 1))
-    l2p = (12 * M + row * G[0] + 4 * M) + (16 * N + row * G[0] + 16 * N)
+    # L2L (parent row read, child row read and written) stops at level 1 when a transform has at
+    # most 8 targets per finest cell (32 at orders >= 7); L2P then also reads the level-1 rows
+    per_cell = 32 if wl.order >= 7 else 8
+
+    def l2l_of(targets):
+        stop = 1 if (len(G) > 1 and targets <= per_cell * G[0]) else 0
+        return sum(row * (G[l + 1] + 2 * G[l]) for l in range(stop, len(G) - 1)), stop == 1
+
+    l2l_f, two_f = l2l_of(M)
+    l2l_b, two_b = l2l_of(N)
+    l2l = l2l_f + l2l_b
+    l2p = (16 * M + row * (G[0] + (G[1] if two_f else 0)) + 4 * M)
+    l2p += (16 * N + row * (G[0] + (G[1] if two_b else 0)) + 16 * N)
     out = {}
     for name, b in (("sort", sort), ("p2m", p2m), ("m2m", m2m), ("l2l", l2l), ("l2p", l2p)):
         ms = m.stage_ms.get(name)
