@@ -15,6 +15,8 @@ Public functions (all arrays are numpy, float64 unless stated):
 * ``backward_q(desc, p, w, q, ybar, sel=None, ...)`` -> qbar (gradient at the queries).
 * ``partials(desc, p, w, q, sel=None, ...)`` -> (value, first partials, second partials) of the
     forward series at the queries (the accessor of Sec. 3, "How to use the implementation?").
+* ``ray_forward(desc, p, w, rays)`` / ``ray_backward(desc, p, w, rays, ybar)`` -> integrals of the
+    series along rays (Sec. 4, integral-implicit layer) and their adjoint (w̄, p̄).
 * ``direct(desc, p, w, q, sel=None)`` -> exact O(NM) sum of Eq. 1.
 * ``kernel_derivs(desc, c)`` -> d^m psi(c), |m| <= order, graded order.
 * ``multi_indices(dim, order)`` -> exponents [P, dim], graded order.
@@ -105,6 +107,12 @@ def _load():
                                             P, ctypes.c_int64,
                                             P, P, P, ctypes.c_int]
             lib.orc_transform_h.restype = ctypes.c_int
+            lib.orc_ray_forward.argtypes = [ctypes.POINTER(_Desc), P, P, ctypes.c_int64, P, P, P, P,
+                                            ctypes.c_int64, P]
+            lib.orc_ray_forward.restype = ctypes.c_int
+            lib.orc_ray_backward.argtypes = [ctypes.POINTER(_Desc), P, P, P, P, P, ctypes.c_int64, P,
+                                             ctypes.c_int64, P, P, P]
+            lib.orc_ray_backward.restype = ctypes.c_int
             lib.orc_direct.argtypes = [ctypes.POINTER(_Desc), P, P, ctypes.c_int64,
                                        P, ctypes.c_int64, P, ctypes.c_int64, P]
             lib.orc_direct.restype = ctypes.c_int
@@ -247,6 +255,52 @@ def partials(desc: OracleDesc, p, w, q, sel=None, src_cell=None, tgt_cell=None, 
     [n, dim(dim+1)/2] for i <= k, row-major), the binning of q held fixed."""
     return transform(desc, p, w, q, sel=sel, src_cell=src_cell, tgt_cell=tgt_cell, want_hess=True,
                      fault=fault)
+
+
+def _rays(rays):
+    """Split rays [R, 8] = (origin (3), direction (3), t0, t1) into contiguous float64 arrays."""
+    r = _f64(rays).reshape(-1, 8)
+    return (np.ascontiguousarray(r[:, 0:3]), np.ascontiguousarray(r[:, 3:6]),
+            np.ascontiguousarray(r[:, 6]), np.ascontiguousarray(r[:, 7]))
+
+
+def ray_forward(desc: OracleDesc, p, w, rays):
+    """Sec. 4, integral-implicit layer: y_q = int_{t0}^{t1} f(o_q + t r_q) dt of the series of (p, w),
+    for rays [R, 8] (origin, direction, t0, t1; the part outside the domain box is dropped), through
+    the cells each ray crosses (line2poly).  3D."""
+    D = desc.dim
+    p = _f64(p).reshape(-1, D)
+    w = _f64(w).reshape(-1)
+    o, r, t0, t1 = _rays(rays)
+    y = np.zeros(o.shape[0], dtype=np.float64)
+    cd = desc.c()
+    rc = _load().orc_ray_forward(ctypes.byref(cd), p.ctypes.data, w.ctypes.data, p.shape[0], o.ctypes.data,
+                                 r.ctypes.data, t0.ctypes.data, t1.ctypes.data, o.shape[0], y.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle ray transform rejected its arguments (rc={rc})")
+    return y
+
+
+def ray_backward(desc: OracleDesc, p, w, rays, ybar, src_cell=None):
+    """Adjoint of ``ray_forward`` for the cotangent ybar [R]: the rays become the sources (ray2M,
+    line2taylor) with weights ybar and p the targets; returns (wbar [N], pbar = w * gradient [N, 3]),
+    the binning of p held fixed when ``src_cell`` is given."""
+    D = desc.dim
+    p = _f64(p).reshape(-1, D)
+    w = _f64(w).reshape(-1)
+    yb = _f64(ybar).reshape(-1)
+    o, r, t0, t1 = _rays(rays)
+    val = np.zeros(p.shape[0], dtype=np.float64)
+    grad = np.zeros((p.shape[0], D), dtype=np.float64)
+    if src_cell is not None:
+        src_cell = np.ascontiguousarray(src_cell, dtype=np.int32)
+    cd = desc.c()
+    rc = _load().orc_ray_backward(ctypes.byref(cd), o.ctypes.data, r.ctypes.data, t0.ctypes.data, t1.ctypes.data,
+                                  yb.ctypes.data, o.shape[0], p.ctypes.data, p.shape[0], _ptr(src_cell),
+                                  val.ctypes.data, grad.ctypes.data)
+    if rc != 0:
+        raise ValueError(f"oracle ray transform rejected its arguments (rc={rc})")
+    return val, grad * w[:, None]
 
 
 def direct(desc: OracleDesc, p, w, q, sel=None):

@@ -329,6 +329,111 @@ static double centre(const orc_desc *d, int nl, int ci) {
     return d->lo + (ci + 0.5) * h;
 }
 
+
+/* ------------------------------------------------------------------- rays
+ * Rays x(t) = o + t r for t in [t0, t1] (Sec. 4, the integral-implicit layer: "Line to
+ * polynomial" and ray2M).  A ray is cut into segments at the faces of the finest cells (the part
+ * outside the domain box is dropped); each segment lies in one cell, found from its midpoint by
+ * the binning rule.  (3D only.) */
+typedef struct { const double *o, *r, *t0, *t1, *wt; int64_t n; } orc_rayset;
+typedef struct { int64_t cell; double ta, tb; } orc_seg;
+
+static int cmp_double(const void *a, const void *b) {
+    const double x = *(const double *)a, y = *(const double *)b;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+/* the segments of one ray (allocated in *out; returns their number) */
+static int64_t ray_segments(const orc_desc *d, const double *o, const double *r, double t0, double t1,
+                            orc_seg **out) {
+    const int D = d->dim, n = d->grid;
+    const double h = (d->hi - d->lo) / n;
+    double ta = t0, tb = t1;
+    *out = NULL;
+    for (int k = 0; k < D; ++k) {          /* clip to the domain box (slabs) */
+        if (r[k] == 0.0) {
+            if (o[k] < d->lo || o[k] >= d->hi) return 0;
+            continue;
+        }
+        double a = (d->lo - o[k]) / r[k], b = (d->hi - o[k]) / r[k];
+        if (a > b) { double tmp = a; a = b; b = tmp; }
+        if (a > ta) ta = a;
+        if (b < tb) tb = b;
+    }
+    if (!(tb > ta)) return 0;
+    double *cut = (double *)malloc(sizeof(double) * (2 + (size_t)D * (n + 1)));
+    int64_t nc = 0;
+    cut[nc++] = ta;
+    for (int k = 0; k < D; ++k) {          /* crossings of the interior faces */
+        if (r[k] == 0.0) continue;
+        for (int j = 1; j < n; ++j) {
+            const double t = (d->lo + j * h - o[k]) / r[k];
+            if (t > ta && t < tb) cut[nc++] = t;
+        }
+    }
+    cut[nc++] = tb;
+    qsort(cut, (size_t)nc, sizeof(double), cmp_double);
+    orc_seg *seg = (orc_seg *)malloc(sizeof(orc_seg) * (size_t)nc);
+    int64_t ns = 0;
+    for (int64_t i = 0; i + 1 < nc; ++i) {
+        if (!(cut[i + 1] > cut[i])) continue;
+        const double tm = 0.5 * (cut[i] + cut[i + 1]);
+        int c[ORC_MAXD];
+        for (int k = 0; k < D; ++k) c[k] = cell_1d(d, n, o[k] + tm * r[k]);
+        seg[ns].cell = ravel(c, n, D);
+        seg[ns].ta = cut[i];
+        seg[ns].tb = cut[i + 1];
+        ++ns;
+    }
+    free(cut);
+    *out = seg;
+    return ns;
+}
+
+/* c[k][i] = dd^(k-i) / (k-i)! * r^i / i!  for i <= k <= rho: the coefficient of tau^i in
+ * (dd + r tau)^k / k!  (binomial theorem) */
+static void line_binomials(double dd, double r, int rho, double c[][ORC_MAXRHO + 1]) {
+    double pd[ORC_MAXRHO + 1], pr[ORC_MAXRHO + 1];
+    powers_over_fact(dd, rho, pd);
+    powers_over_fact(r, rho, pr);
+    for (int k = 0; k <= rho; ++k)
+        for (int i = 0; i <= rho; ++i) c[k][i] = i <= k ? pd[k - i] * pr[i] : 0.0;
+}
+
+/* line2taylor: the moments of a segment entering the cell at dd (relative to its centre) along r
+ * for a length s of the parameter,  out(n) = int_0^s prod_k (dd_k + r_k tau)^(n_k) / n_k! dtau
+ * = sum_{i <= n} prod_k [dd_k^(n_k-i_k)/(n_k-i_k)! r_k^(i_k)/i_k!] s^(|i|+1) / (|i|+1) */
+static void line2taylor(const orc_index *ix, int rho, const double *dd, const double *r, double s, double *out) {
+    double c[3][ORC_MAXRHO + 1][ORC_MAXRHO + 1];
+    for (int k = 0; k < 3; ++k) line_binomials(dd[k], r[k], rho, c[k]);
+    double sp[3 * ORC_MAXRHO + 2];
+    sp[0] = 1.0;
+    for (int m = 1; m < 3 * ORC_MAXRHO + 2; ++m) sp[m] = sp[m - 1] * s;
+    for (int a = 0; a < ix->P; ++a) {
+        const int n1 = ix->ex[a * 3], n2 = ix->ex[a * 3 + 1], n3 = ix->ex[a * 3 + 2];
+        double acc = 0.0;
+        for (int i = 0; i <= n1; ++i)
+            for (int j = 0; j <= n2; ++j)
+                for (int k = 0; k <= n3; ++k)
+                    acc += c[0][n1][i] * c[1][n2][j] * c[2][n3][k] * sp[i + j + k + 1] / (i + j + k + 1);
+        out[a] = acc;
+    }
+}
+
+/* line2poly: the local series L of a cell restricted to the line dd + r x, as a polynomial
+ * sum_m a_m x^m (m <= rho):  a_m = sum_n L(n) sum_{i + j + k = m} prod [dd^(n-i)/(n-i)! r^i/i!] */
+static void line2poly(const orc_index *ix, int rho, const double *L, const double *dd, const double *r, double *a) {
+    double c[3][ORC_MAXRHO + 1][ORC_MAXRHO + 1];
+    for (int k = 0; k < 3; ++k) line_binomials(dd[k], r[k], rho, c[k]);
+    for (int m = 0; m <= rho; ++m) a[m] = 0.0;
+    for (int b = 0; b < ix->P; ++b) {
+        const int n1 = ix->ex[b * 3], n2 = ix->ex[b * 3 + 1], n3 = ix->ex[b * 3 + 2];
+        for (int i = 0; i <= n1; ++i)
+            for (int j = 0; j <= n2; ++j)
+                for (int k = 0; k <= n3; ++k) a[i + j + k] += L[b] * c[0][n1][i] * c[1][n2][j] * c[2][n3][k];
+    }
+}
+
 static int near_idx(const int *a, const int *b, int D) {
     for (int i = 0; i < D; ++i) if (abs(a[i] - b[i]) > 1) return 0;
     return 1;
@@ -365,13 +470,15 @@ static int in_list(const int *s, const int *t, int D, int level, int top, int fa
  * (the accessor's second partials, Sec. 3, "How to use the implementation?").
  * Returns 0 on success, negative on bad arguments.
  */
-int orc_transform_h(const orc_desc *d,
+static int pipeline(const orc_desc *d,
                     const double *src, const double *wt, int64_t n_src, const int32_t *src_cell,
+                    const orc_rayset *src_rays,
                     const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
-                    const int64_t *sel, int64_t n_sel,
-                    double *val, double *grad, double *hess, int fault) {
+                    const int64_t *sel, int64_t n_sel, const orc_rayset *tgt_rays,
+                    double *val, double *grad, double *hess, double *ray_val, int fault) {
     int D = d->dim, n = d->grid, rho = d->order;
     if (D < 2 || D > 3 || n < 4 || (n & (n - 1)) || rho < 0 || rho > ORC_MAXRHO) return -1;
+    if ((src_rays || tgt_rays) && D != 3) return -1;
     if (!(d->hi > d->lo)) return -1;
     orc_index ix;
     index_init(&ix, D, rho);
@@ -401,6 +508,27 @@ int orc_transform_h(const orc_desc *d,
         double pw[ORC_MAXD][ORC_MAXRHO + 1];
         for (int k = 0; k < D; ++k) powers_over_fact(src[i * D + k] - centre(d, n, c[k]), rho, pw[k]);
         for (int b = 0; b < P; ++b) Mx[0][lin * P + b] += wt[i] * mono(&ix, b, pw);
+    }
+
+    /* ---- ray2M (Sec. 4): every segment of a source ray adds its weight times line2taylor to the
+     * moments of its cell, entry point taken relative to the cell centre */
+    if (src_rays) {
+        double *mt = (double *)malloc(sizeof(double) * P);
+        for (int64_t q = 0; q < src_rays->n; ++q) {
+            orc_seg *seg;
+            const double *o = src_rays->o + 3 * q, *r = src_rays->r + 3 * q;
+            const int64_t ns = ray_segments(d, o, r, src_rays->t0[q], src_rays->t1[q], &seg);
+            for (int64_t g = 0; g < ns; ++g) {
+                int c[ORC_MAXD];
+                unravel(seg[g].cell, n, D, c);
+                double dd[3];
+                for (int k = 0; k < 3; ++k) dd[k] = o[k] + seg[g].ta * r[k] - centre(d, n, c[k]);
+                line2taylor(&ix, rho, dd, r, seg[g].tb - seg[g].ta, mt);
+                for (int b = 0; b < P; ++b) Mx[0][seg[g].cell * P + b] += src_rays->wt[q] * mt[b];
+            }
+            free(seg);
+        }
+        free(mt);
     }
 
     /* ---- M2M: script-M(n, p'') = sum_{p' in I(p'')} sum_{k <= n} d'^(n-k)/(n-k)! script-M(k, p') */
@@ -445,6 +573,14 @@ int orc_transform_h(const orc_desc *d,
         tcell[j] = (int32_t)lin;
         need[0][lin] = 1;
     }
+    if (tgt_rays)
+        for (int64_t q = 0; q < tgt_rays->n; ++q) {
+            orc_seg *seg;
+            const int64_t ns = ray_segments(d, tgt_rays->o + 3 * q, tgt_rays->r + 3 * q, tgt_rays->t0[q],
+                                            tgt_rays->t1[q], &seg);
+            for (int64_t g = 0; g < ns; ++g) need[0][seg[g].cell] = 1;
+            free(seg);
+        }
     for (int l = 0; l + 1 < nlev; ++l) {
         int nl = n >> l;
         for (int64_t c = 0; c < G[l]; ++c) if (need[l][c]) {
@@ -593,10 +729,41 @@ int orc_transform_h(const orc_desc *d,
         }
     }
 
+    /* ---- ray integrals (Sec. 4): each segment's cell series restricted to the line (line2poly),
+     * integrated over the segment: int_0^s sum_m a_m x^m dx = sum_m a_m s^(m+1) / (m+1) */
+    if (tgt_rays)
+        for (int64_t q = 0; q < tgt_rays->n; ++q) {
+            orc_seg *seg;
+            const double *o = tgt_rays->o + 3 * q, *r = tgt_rays->r + 3 * q;
+            const int64_t ns = ray_segments(d, o, r, tgt_rays->t0[q], tgt_rays->t1[q], &seg);
+            double acc = 0.0;
+            for (int64_t g = 0; g < ns; ++g) {
+                int c[ORC_MAXD];
+                unravel(seg[g].cell, n, D, c);
+                double dd[3], a[ORC_MAXRHO + 1];
+                for (int k = 0; k < 3; ++k) dd[k] = o[k] + seg[g].ta * r[k] - centre(d, n, c[k]);
+                line2poly(&ix, rho, Lx[0] + seg[g].cell * P, dd, r, a);
+                const double s = seg[g].tb - seg[g].ta;
+                double sp = s;
+                for (int m = 0; m <= rho; ++m, sp *= s) acc += a[m] * sp / (m + 1);
+            }
+            ray_val[q] = acc;
+            free(seg);
+        }
+
     free(tcell);
     for (int l = 0; l < nlev; ++l) { free(Mx[l]); free(Lx[l]); free(need[l]); }
     index_free(&ix);
     return 0;
+}
+
+int orc_transform_h(const orc_desc *d,
+                    const double *src, const double *wt, int64_t n_src, const int32_t *src_cell,
+                    const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
+                    const int64_t *sel, int64_t n_sel,
+                    double *val, double *grad, double *hess, int fault) {
+    return pipeline(d, src, wt, n_src, src_cell, NULL, tgt, n_tgt, tgt_cell, sel, n_sel, NULL, val, grad, hess, NULL,
+                    fault);
 }
 
 int orc_transform(const orc_desc *d,
@@ -605,6 +772,27 @@ int orc_transform(const orc_desc *d,
                   const int64_t *sel, int64_t n_sel,
                   double *val, double *grad, int fault) {
     return orc_transform_h(d, src, wt, n_src, src_cell, tgt, n_tgt, tgt_cell, sel, n_sel, val, grad, NULL, fault);
+}
+
+/* Ray integrals of the transform (Sec. 4, integral-implicit layer), rays given by origins o and
+ * directions r [n_ray][3] and parameter ranges [t0, t1] (clipped to the domain box):
+ *   forward:  y_q = int_{t0}^{t1} f(o_q + t r_q) dt,  f the series of (src, wt)  (line2poly);
+ *   backward: value (and gradient) at the targets of the transform whose sources are the rays with
+ *             weights ybar (ray2M with line2taylor), i.e. wbar_n = sum_q ybar_q int T(p_n, x_q(t)) dt
+ *             and, times w_n, pbar_n. */
+int orc_ray_forward(const orc_desc *d, const double *src, const double *wt, int64_t n_src,
+                    const double *o, const double *r, const double *t0, const double *t1, int64_t n_ray,
+                    double *y) {
+    orc_rayset rs = {o, r, t0, t1, NULL, n_ray};
+    return pipeline(d, src, wt, n_src, NULL, NULL, NULL, 0, NULL, NULL, 0, &rs, NULL, NULL, NULL, y, ORC_FAULT_NONE);
+}
+
+int orc_ray_backward(const orc_desc *d, const double *o, const double *r, const double *t0, const double *t1,
+                     const double *ybar, int64_t n_ray, const double *tgt, int64_t n_tgt, const int32_t *tgt_cell,
+                     double *val, double *grad) {
+    orc_rayset rs = {o, r, t0, t1, ybar, n_ray};
+    return pipeline(d, NULL, NULL, 0, NULL, &rs, tgt, n_tgt, tgt_cell, NULL, -1, NULL, val, grad, NULL, NULL,
+                    ORC_FAULT_NONE);
 }
 
 /* Exact O(N M) sum of Eq. 1 at the selected targets (accuracy reference). */

@@ -440,3 +440,136 @@ def test_each_planted_mistake_fails_a_pin(fault):
     yp = oracle.forward(dp, p, w, q, fault=fault)
     caught.append(np.max(np.abs(yp - oracle.direct(dp, p, w, q))) > 1e-9)
     assert any(caught), fault
+
+
+# ---------------------------------------------------------------- rays (Sec. 4, integral layer)
+
+def _clip(o, r, t0, t1, lo=0.0, hi=1.0):
+    """Parameter range of o + t r inside [lo, hi)^3 within [t0, t1] (slab method), or None."""
+    ta, tb = t0, t1
+    for k in range(3):
+        if r[k] == 0.0:
+            if not (lo <= o[k] < hi):
+                return None
+            continue
+        a, b = (lo - o[k]) / r[k], (hi - o[k]) / r[k]
+        ta, tb = max(ta, min(a, b)), min(tb, max(a, b))
+    return (ta, tb) if tb > ta else None
+
+
+def _rays(seed, R, spread=1.0):
+    rng = np.random.default_rng(seed)
+    o = rng.random((R, 3)) * spread - 0.5 * (spread - 1.0)
+    d = rng.standard_normal((R, 3))
+    t0 = -rng.random(R) * 0.5
+    t1 = rng.random(R) * 0.8
+    return np.concatenate([o, d, t0[:, None], t1[:, None]], axis=1)
+
+
+def _direct_ray(desc, p, w, rays, nodes=24):
+    """Exact line integral of the direct sum for a polynomial kernel: Gauss-Legendre on the
+    clipped range with enough nodes for its degree."""
+    x, wq = np.polynomial.legendre.leggauss(nodes)
+    out = np.zeros(rays.shape[0])
+    for i, ray in enumerate(rays):
+        rng_ = _clip(ray[:3], ray[3:6], ray[6], ray[7])
+        if rng_ is None:
+            continue
+        ta, tb = rng_
+        t = 0.5 * (tb - ta) * (x + 1.0) + ta
+        q = ray[None, :3] + t[:, None] * ray[None, 3:6]
+        out[i] = 0.5 * (tb - ta) * float(wq @ oracle.direct(desc, p, w, q))
+    return out
+
+
+@pytest.mark.parametrize("name", ["one", "r2", "one_minus_r2_sq", "odd_mixed"])
+def test_ray_integral_polynomial_exact(name):
+    """For psi a polynomial of degree <= rho the series is the field, so the integral of the series
+    along a ray (cut at the cells it crosses, each cell's series restricted to the line) equals the
+    integral of the direct sum; psi = 1 gives sum(w) times the length inside the domain."""
+    terms = POLYS_3D[name]
+    deg = max(sum(m) for m in terms)
+    coef = poly_coef(terms, 3, deg)
+    d = oracle.OracleDesc(dim=3, grid=8, order=max(deg, 4), kernel="poly", poly_coef=coef)
+    p, w, _ = small_inputs(140, 3, 40, 1)
+    rays = _rays(141, 25, spread=1.4)
+    y = oracle.ray_forward(d, p, w, rays)
+    ref = _direct_ray(d, p, w, rays)
+    assert np.max(np.abs(y - ref)) <= 1e-10 * max(1.0, np.abs(ref).max()), name
+
+
+def _gauss_ray_closed_form(p, w, rays, sigma):
+    """int exp(-|p - o - t r|^2 / (2 sigma^2)) dt over the clipped range, by completing the square:
+    exp(-c / (2 sigma^2)) sigma sqrt(pi/2) / |r| [erf(|r| (tb - t*) / (sigma sqrt 2)) - erf(..ta..)]."""
+    from math import erf, sqrt, pi, exp
+    out = np.zeros(rays.shape[0])
+    for i, ray in enumerate(rays):
+        rng_ = _clip(ray[:3], ray[3:6], ray[6], ray[7])
+        if rng_ is None:
+            continue
+        ta, tb = rng_
+        o, r = ray[:3], ray[3:6]
+        rr = float(r @ r)
+        acc = 0.0
+        for pn, wn in zip(p, w):
+            v = pn - o
+            ts = float(r @ v) / rr
+            c = float(v @ v) - float(r @ v) ** 2 / rr
+            a = sqrt(rr) / (sigma * sqrt(2.0))
+            acc += wn * exp(-c / (2 * sigma ** 2)) * sigma * sqrt(pi / 2) / sqrt(rr) * (erf(a * (tb - ts)) - erf(a * (ta - ts)))
+        out[i] = acc
+    return out
+
+
+def test_ray_integral_gaussian_closed_form_and_decay():
+    """Gaussian kernel: the series' ray integral approaches the closed-form line integral of the
+    direct sum (erf), with the error falling as the order rises."""
+    p, w, _ = small_inputs(150, 3, 60, 1)
+    rays = _rays(151, 30)
+    sigma = 0.15
+    ref = _gauss_ray_closed_form(p, w, rays, sigma)
+    errs = []
+    for order in (2, 4, 6, 8):
+        d = oracle.OracleDesc(dim=3, grid=8, order=order, sigma=sigma)
+        errs.append(rel(oracle.ray_forward(d, p, w, rays), ref))
+    assert errs[-1] <= 2e-3, errs
+    assert all(b < a for a, b in zip(errs, errs[1:])), errs
+
+
+def test_ray_adjoint_identity_and_linearity():
+    """<ybar, F(w)> = <F^T(ybar), w> between the ray integral (line2poly) and its adjoint (ray2M
+    with line2taylor), which are computed by different formulas; rays wholly outside or of zero
+    length contribute nothing."""
+    p, w, _ = small_inputs(160, 3, 50, 1)
+    rays = _rays(161, 40, spread=1.5)
+    rays[0, 6:8] = [0.3, 0.3]                       # zero length
+    rays[1, :6] = [2.0, 2.0, 2.0, 1.0, 0.0, 0.0]   # outside the domain
+    ybar = np.random.default_rng(162).standard_normal(40)
+    d = oracle.OracleDesc(dim=3, grid=8, order=5, sigma=0.12)
+    y = oracle.ray_forward(d, p, w, rays)
+    wbar, _ = oracle.ray_backward(d, p, w, rays, ybar)
+    assert y[0] == 0.0 and y[1] == 0.0
+    assert abs(float(ybar @ y) - float(wbar @ w)) <= 1e-12 * (np.abs(ybar) @ np.abs(y))
+    y2 = oracle.ray_forward(d, p, 2.0 * w + 1.0, rays)
+    y1 = oracle.ray_forward(d, p, np.ones_like(w), rays)
+    assert np.max(np.abs(y2 - (2.0 * y + y1))) <= 1e-12 * np.abs(y2).max()
+
+
+def test_ray_source_gradient_vs_central_differences():
+    """pbar of the ray adjoint against central differences of L = <ybar, F(p)> in the source
+    positions (sources kept away from cell faces so the binning does not change)."""
+    d = oracle.OracleDesc(dim=3, grid=8, order=4, sigma=0.12)
+    rng = np.random.default_rng(170)
+    p = (rng.integers(0, 8, (20, 3)) + 0.2 + 0.6 * rng.random((20, 3))) / 8.0
+    w = rng.standard_normal(20)
+    rays = _rays(171, 30)
+    ybar = rng.standard_normal(30)
+    _, pbar = oracle.ray_backward(d, p, w, rays, ybar)
+    for n in range(0, 20, 4):
+        for k in range(3):
+            eps = 1e-5
+            pp, pm = p.copy(), p.copy()
+            pp[n, k] += eps
+            pm[n, k] -= eps
+            fd = (ybar @ oracle.ray_forward(d, pp, w, rays) - ybar @ oracle.ray_forward(d, pm, w, rays)) / (2 * eps)
+            assert abs(fd - pbar[n, k]) <= 1e-6 * (np.abs(pbar).max() + 1e-30), (n, k, fd, pbar[n, k])
