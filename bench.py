@@ -429,6 +429,55 @@ def stage_roofline(m: Measured, wl, peaks):
     return out
 
 
+def measure_rays(dev, flush, steps, warmup):
+    """Ray integrals (Sec. 4, integral-implicit layer) on the ray workload's sizes: 2^18 sphere-surface
+    sources, the 512 x 512 pixel rays of its pinhole camera through the cube, 64^3, order 8, sigma
+    0.01, separable M2L; a step is the forward ray integrals and their adjoint (wbar, pbar for
+    L = sum y^2 / 2), timed with CUDA events on the launching stream."""
+    import torch
+    from paper_2111_00110_gb300 import workloads
+    from paper_2111_00110_gb300.transform import Plan
+    src = workloads.sphere_rays(width=4, height=4, samples=1)
+    rays = torch.from_numpy(workloads.pinhole_rays(512, 512)).to(dev)
+    p = torch.from_numpy(src.p).to(dev)
+    w = torch.from_numpy(src.w).to(dev)
+    plan = Plan(3, src.grid, src.order, src.sigma, m2l="separable", max_sources=src.N, max_queries=1, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        y = plan.ray_forward(p, w, rays)
+        plan.ray_backward(p, w, rays, y)
+
+    for _ in range(max(3, warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    plan.profile_read(reset=True)
+    total = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        total += a.elapsed_time(b)
+    _, launches = plan.profile_read(reset=True)
+    plan.profile(True)
+    step()
+    torch.cuda.synchronize(dev)
+    stage_ms, _ = plan.profile_read(reset=True)
+    plan.profile(False)
+    R = rays.shape[0]
+    ms = total / steps
+    out = {"workload": "sphere_rays sources, 512x512 pinhole rays", "N": src.N, "rays": R, "grid": src.grid,
+           "order": src.order, "sigma": src.sigma, "m2l": "separable", "value": R / (ms / 1e3),
+           "unit": "rays/s (ray integrals + adjoint)", "ms_per_step": ms, "steps": steps,
+           "gpu_launches": int(sum(launches.values())),
+           "stage_ms_per_step": {k: v for k, v in stage_ms.items() if v}}
+    plan.close()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -450,6 +499,7 @@ def run_ours(args, rank, world, local_rank):
     if args.m2l == "auto":
         for mode in ("bf16x3", "tf32x3", "tf32", "bf16", "fp32"):
             variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref, steps=min(args.steps, 10))
+    rays = measure_rays(dev, flush, min(args.steps, 10), args.warmup) if (args.m2l == "auto" and rank == 0) else None
     if rank != 0:
         return
     peaks = load_peaks()
@@ -489,6 +539,7 @@ def run_ours(args, rank, world, local_rank):
                            "stages": stage_roofline(main, wl, peaks)},
         "stage_ms_per_step": main.stage_ms,
         "variants": {k: summary(v) for k, v in variants.items()},
+        "ray_integrals": rays,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

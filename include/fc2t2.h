@@ -223,6 +223,31 @@ FC2T2_API fc2t2_status fc2t2_evaluate(fc2t2_plan plan, void *stream, const float
 FC2T2_API fc2t2_status fc2t2_evaluate_grid(fc2t2_plan plan, void *stream, const float *const *axis,
                                            const int64_t *count, fc2t2_eval what, float *out);
 
+/* ---- Ray integrals (Sec. 4, the integral-implicit layer: a transform integrated along rays, the
+ * building block of the paper's rendering and ray-sampled losses).  Rays are R records of 8
+ * floats [R][8]: origin o (3), direction r (3), t0, t1; ray q covers x(t) = o + t r for t in
+ * [t0, t1] (the parameter, not arc length, is integrated), clipped to the domain box [lo, hi)^3.
+ * A ray is cut at the faces of the finest cells it crosses and each segment is integrated exactly
+ * (up to rounding) with the series of the cell that holds it (the cell of its midpoint by the
+ * binning rule), by Gauss-Legendre quadrature with ceil((order + 1) / 2) nodes.  3D plans only
+ * (UNSUPPORTED otherwise). */
+
+/* y[c][q] = int_{t0}^{t1} f_c(o_q + t r_q) dt,  f_c the series of (p, w[c]).  Any R >= 0 (no
+ * workspace bound).  Errors: INVALID_ARG, UNSUPPORTED, DOMAIN (check_domain, for p), CUDA. */
+FC2T2_API fc2t2_status fc2t2_ray_forward(fc2t2_plan plan, void *stream, const float *p, const float *w,
+                                         int64_t N, const float *rays, int64_t R, float *y);
+
+/* The adjoint of fc2t2_ray_forward for a cotangent ybar [C][R]: the rays become the sources, each
+ * segment adding ybar_q times its integral of the scaled monomials to its cell's moments (the
+ * paper's ray2M), and the transform is evaluated and differentiated at the sources p:
+ *   wbar[c][n] = sum_q ybar[c][q] int T(p_n, x_q(t)) dt,
+ *   pbar[n][i] = sum_c w[c][n] d/dp_{n,i} (the same),  T the series' kernel.
+ * The moments are summed with float atomics (rays in any order): results are reproducible to
+ * rounding, not bit for bit.  Either output may be NULL.  Errors: as fc2t2_ray_forward. */
+FC2T2_API fc2t2_status fc2t2_ray_backward(fc2t2_plan plan, void *stream, const float *p, const float *w,
+                                          int64_t N, const float *rays, int64_t R, const float *ybar,
+                                          float *wbar, float *pbar);
+
 /* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
  * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,
  * each of n_inst entries) with N[i] sources and M[i] queries.  All instances are enqueued on

@@ -47,6 +47,8 @@ EXPORTS = (
     "fc2t2_expand",
     "fc2t2_evaluate",
     "fc2t2_evaluate_grid",
+    "fc2t2_ray_forward",
+    "fc2t2_ray_backward",
 )
 # what fc2t2_evaluate returns per point and channel
 EVAL = {"value": 0, "partials": 1, "partials2": 2}
@@ -126,6 +128,8 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_expand.argtypes = [vp, vp, vp, vp, i64]
         lib.fc2t2_evaluate.argtypes = [vp, vp, vp, i64, ctypes.c_int, vp]
         lib.fc2t2_evaluate_grid.argtypes = [vp, vp, vp, vp, ctypes.c_int, vp]
+        lib.fc2t2_ray_forward.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp]
+        lib.fc2t2_ray_backward.argtypes = [vp, vp, vp, vp, i64, vp, i64, vp, vp, vp]
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
@@ -187,6 +191,17 @@ def evaluate_grid(plan: int, stream: int, axes, counts, what: str, out: int) -> 
     ax = (ctypes.c_void_p * len(axes))(*[a or None for a in axes])
     n = (ctypes.c_int64 * len(counts))(*counts)
     check(load().fc2t2_evaluate_grid(plan, stream, ctypes.addressof(ax), ctypes.addressof(n), EVAL[what], out))
+
+
+def ray_forward(plan: int, stream: int, p: int, w: int, N: int, rays: int, R: int, y: int) -> None:
+    """Integrals of the series along R rays [R][8] (device pointers)."""
+    check(load().fc2t2_ray_forward(plan, stream, p, w, N, rays, R, y))
+
+
+def ray_backward(plan: int, stream: int, p: int, w: int, N: int, rays: int, R: int, ybar: int, wbar: int,
+                 pbar: int) -> None:
+    """Adjoint of ray_forward: (wbar, pbar) at the sources for the cotangent ybar (device pointers)."""
+    check(load().fc2t2_ray_backward(plan, stream, p, w, N, rays, R, ybar, wbar, pbar))
 
 
 def direct(desc: PlanDesc, stream: int, p: int, w: int, N: int, q: int, M: int, y: int) -> None:

@@ -412,11 +412,11 @@ static fc2t2_status evaluate_targets(fc2t2_plan_s *pl, cudaStream_t s, const Sor
 // P2M .. M2L .. L2L: expansion of sorted sources into local coefficients: with l2l, the finest
 // level's rows of d_L hold the whole local series; without, L2L stops at level 1 and the finest
 // level's rows hold its own M2L only (for launch_l2p_two)
-static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &src, bool l2l = true) {
+static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork *src, bool l2l = true) {
     fc2t2_status st;
-    {
+    if (src) {   // (NULL: the finest moments are already in place, e.g. from ray2M)
         StageScope scope(pl, s, FC2T2_STAGE_P2M);
-        if ((st = check_cuda(launch_p2m(pl, s, src, pl->d_M), "p2m")) != FC2T2_OK) return st;
+        if ((st = check_cuda(launch_p2m(pl, s, *src, pl->d_M), "p2m")) != FC2T2_OK) return st;
     }
     if (forks(pl)) {
         // The finest level's M2L needs only the finest moments; everything above it (M2M, the
@@ -569,7 +569,7 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
     const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, y + (int64_t)c * M, nullptr, false)) != FC2T2_OK)
             return st;
@@ -604,7 +604,7 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
             if (pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, pl->qry, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->qry, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         // pbar sums the channels' contributions w[c] * grad g_c
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
@@ -633,7 +633,7 @@ fc2t2_status fc2t2_backward_reuse(fc2t2_plan pl, void *stream, const float *p, c
         if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         // (one channel: the sort of p still carries w)
         if (C > 1 && pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, pl->qry, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->qry, !two)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
             FC2T2_OK)
             return st;
@@ -667,12 +667,69 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
             if ((st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, nullptr, qbar, c > 0)) != FC2T2_OK) return st;
     }
     pl->src.held_w = w;
     pl->qry.held_w = ybar;
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_ray_forward(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                               const float *rays, int64_t R, float *y) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->D != 3) return set_error(FC2T2_ERR_UNSUPPORTED, "ray integrals need dim = 3");
+    if (N < 0 || N > pl->src.cap || R < 0) return set_error(FC2T2_ERR_INVALID_ARG, "N outside [0, max_sources] or R < 0");
+    if (R == 0) return FC2T2_OK;
+    if (!rays || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
+    fc2t2_status st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
+    if (N == 0) return check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * R * C, s), "zero y");
+    if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    for (int c = 0; c < C; ++c) {
+        if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, true)) != FC2T2_OK) return st;   // the finest series, complete
+        StageScope scope(pl, s, FC2T2_STAGE_L2P);
+        if ((st = check_cuda(launch_ray_forward(pl, s, rays, R, y + (int64_t)c * R), "ray integrals")) != FC2T2_OK)
+            return st;
+    }
+    pl->src.held_w = w;
+    return finish_flags(pl, s);
+}
+
+fc2t2_status fc2t2_ray_backward(fc2t2_plan pl, void *stream, const float *p, const float *w, int64_t N,
+                                const float *rays, int64_t R, const float *ybar, float *wbar, float *pbar) {
+    if (!pl) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    if (pl->D != 3) return set_error(FC2T2_ERR_UNSUPPORTED, "ray integrals need dim = 3");
+    if (N < 0 || N > pl->src.cap || R < 0) return set_error(FC2T2_ERR_INVALID_ARG, "N outside [0, max_sources] or R < 0");
+    if (N == 0 || (!wbar && !pbar)) return FC2T2_OK;
+    if (!p || !w || (R > 0 && (!rays || !ybar))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int C = pl->C;
+    fc2t2_status st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
+    // the transposed transform: sources = the rays with weights ybar (ray2M), targets p
+    if ((st = sort_targets(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
+    const bool two = l2p_two_levels(pl, N);
+    const size_t mbytes = sizeof(float) * (size_t)pl->lev[0].G * pl->Pp;
+    for (int c = 0; c < C; ++c) {
+        if (c > 0 && pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
+        {
+            StageScope scope(pl, s, FC2T2_STAGE_P2M);
+            if ((st = check_cuda(cudaMemsetAsync(pl->d_M, 0, mbytes, s), "zero moments")) != FC2T2_OK) return st;
+            if ((st = check_cuda(launch_ray2m(pl, s, rays, R, ybar + (int64_t)c * R, pl->d_M), "ray2M")) != FC2T2_OK)
+                return st;
+        }
+        if ((st = expand(pl, s, nullptr, !two)) != FC2T2_OK) return st;
+        if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
+        if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
+            FC2T2_OK)
+            return st;
+    }
+    pl->src.held_w = w;
     return finish_flags(pl, s);
 }
 
@@ -695,7 +752,7 @@ fc2t2_status fc2t2_expand(fc2t2_plan pl, void *stream, const float *p, const flo
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src)) != FC2T2_OK) return st;
         // (one channel: the finest level of d_L is the held expansion)
         if (C > 1 && (st = check_cuda(cudaMemcpyAsync(hold + (size_t)c * row_floats, pl->d_L, sizeof(float) * row_floats,
                                                       cudaMemcpyDeviceToDevice, s),

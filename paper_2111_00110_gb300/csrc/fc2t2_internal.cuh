@@ -68,6 +68,50 @@ __device__ __forceinline__ void power_ladder(float u, float (&pw)[RHO + 1]) {
     for (int k = 1; k <= RHO; ++k) pw[k] = pw[k - 1] * (u * (1.0f / (float)k));
 }
 
+// The series of one coefficient row at u (power ladders pw): value, and with GRAD the three
+// sums of the shifted rows sum_k Lt(k + e_i) u^k / k! (the gradient in u), nested over the
+// exponents; the results are added to value, g[].
+template <int D, int RHO, bool GRAD>
+__device__ __forceinline__ void series_add(const float *Lv, const float (&pw)[3][RHO + 1], float &value,
+                                           float (&g)[3]) {
+    float val = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
+#pragma unroll
+    for (int a0 = 0; a0 <= RHO; ++a0) {
+        float U = 0.0f, U1 = 0.0f, U2 = 0.0f;
+#pragma unroll
+        for (int a1 = 0; a1 <= RHO; ++a1) {
+            if (a0 + a1 > RHO) continue;
+            float T = 0.0f, T2 = 0.0f;
+            if (D == 2) {
+                T = Lv[gidx2(a0, a1)];
+            } else {
+#pragma unroll
+                for (int a2 = 0; a2 <= RHO; ++a2) {
+                    if (a0 + a1 + a2 > RHO) continue;
+                    const float l = Lv[gidx3(a0, a1, a2)];
+                    T = fmaf(pw[2][a2], l, T);
+                    if (GRAD && a2 >= 1) T2 = fmaf(pw[2][a2 - 1], l, T2);
+                }
+            }
+            U = fmaf(pw[1][a1], T, U);
+            if (GRAD) {
+                if (a1 >= 1) U1 = fmaf(pw[1][a1 - 1], T, U1);
+                if (D == 3) U2 = fmaf(pw[1][a1], T2, U2);
+            }
+        }
+        val = fmaf(pw[0][a0], U, val);
+        if (GRAD) {
+            if (a0 >= 1) g0 = fmaf(pw[0][a0 - 1], U, g0);
+            g1 = fmaf(pw[0][a0], U1, g1);
+            if (D == 3) g2 = fmaf(pw[0][a0], U2, g2);
+        }
+    }
+    value += val;
+    g[0] += g0;
+    g[1] += g1;
+    g[2] += g2;
+}
+
 // One counting sort of points into finest-level cells.
 struct SortWork {
     int64_t cap = 0;
@@ -188,6 +232,11 @@ cudaError_t launch_l2p(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
 // complete local series, both about the point's cells (needs two or more levels)
 cudaError_t launch_l2p_two(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,
                            float *val, float *grad_times_w, bool accumulate = false);
+// ray integrals (3D): rays [R][8] = (origin, direction, t0, t1); y[q] = the integral of the
+// finest-level series along ray q; ray2M adds ybar_q times the rays' moment integrals to M0
+cudaError_t launch_ray_forward(const fc2t2_plan_s *pl, cudaStream_t s, const float *rays, int64_t R, float *y);
+cudaError_t launch_ray2m(const fc2t2_plan_s *pl, cudaStream_t s, const float *rays, int64_t R, const float *ybar,
+                         float *M0);
 // the accessor: channels [C] of finest-level locals L (channel stride G0 * Pp) evaluated at the
 // sorted points of w (out [C][m][K]) or on the meshgrid of axis[0..D-1] (out [C][n0][n1]([n2])[K])
 cudaError_t launch_eval_sorted(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, int64_t m,

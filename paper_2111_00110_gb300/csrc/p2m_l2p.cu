@@ -97,50 +97,6 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
 
 constexpr int kL2PThreads = 128;
 
-// The series of one coefficient row at u (power ladders pw): value, and with GRAD the three
-// sums of the shifted rows sum_k Lt(k + e_i) u^k / k! (the gradient in u), nested over the
-// exponents; the results are added to value, g[].
-template <int D, int RHO, bool GRAD>
-__device__ __forceinline__ void series_add(const float *Lv, const float (&pw)[3][RHO + 1], float &value,
-                                           float (&g)[3]) {
-    float val = 0.0f, g0 = 0.0f, g1 = 0.0f, g2 = 0.0f;
-#pragma unroll
-    for (int a0 = 0; a0 <= RHO; ++a0) {
-        float U = 0.0f, U1 = 0.0f, U2 = 0.0f;
-#pragma unroll
-        for (int a1 = 0; a1 <= RHO; ++a1) {
-            if (a0 + a1 > RHO) continue;
-            float T = 0.0f, T2 = 0.0f;
-            if (D == 2) {
-                T = Lv[gidx2(a0, a1)];
-            } else {
-#pragma unroll
-                for (int a2 = 0; a2 <= RHO; ++a2) {
-                    if (a0 + a1 + a2 > RHO) continue;
-                    const float l = Lv[gidx3(a0, a1, a2)];
-                    T = fmaf(pw[2][a2], l, T);
-                    if (GRAD && a2 >= 1) T2 = fmaf(pw[2][a2 - 1], l, T2);
-                }
-            }
-            U = fmaf(pw[1][a1], T, U);
-            if (GRAD) {
-                if (a1 >= 1) U1 = fmaf(pw[1][a1 - 1], T, U1);
-                if (D == 3) U2 = fmaf(pw[1][a1], T2, U2);
-            }
-        }
-        val = fmaf(pw[0][a0], U, val);
-        if (GRAD) {
-            if (a0 >= 1) g0 = fmaf(pw[0][a0 - 1], U, g0);
-            g1 = fmaf(pw[0][a0], U1, g1);
-            if (D == 3) g2 = fmaf(pw[0][a0], U2, g2);
-        }
-    }
-    value += val;
-    g[0] += g0;
-    g[1] += g1;
-    g[2] += g2;
-}
-
 // the outputs of one point: val[i] = value; grad[i] = (or += with accumulate) scale * g
 template <int D, bool GRAD>
 __device__ __forceinline__ void l2p_store(int64_t i, float value, const float (&g)[3], float scale, float *val,

@@ -158,6 +158,58 @@ class Plan:
         capi.backward_q(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(q), M, _ptr(ybar), _ptr(qbar))
         return qbar
 
+    def ray_forward(self, p: torch.Tensor, w: torch.Tensor, rays: torch.Tensor) -> torch.Tensor:
+        """Integrals of the series of (p, w) along rays [R, 8] = (origin, direction, t0, t1):
+        y[c, q] = int_{t0}^{t1} f_c(o_q + t r_q) dt (Sec. 4, the integral-implicit layer)."""
+        N, R = p.shape[0], rays.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", self._chan_shape(w, N))
+        _check_tensor(rays, "rays", (R, 8))
+        y = torch.empty(self._chan_shape(w, R), device=p.device, dtype=torch.float32)
+        self._serial += 1
+        capi.ray_forward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(rays), R, _ptr(y))
+        return y
+
+    def ray_backward(self, p: torch.Tensor, w: torch.Tensor, rays: torch.Tensor, ybar: torch.Tensor,
+                     need_w: bool = True, need_p: bool = True):
+        """(wbar, pbar) of ``ray_forward`` for the cotangent ybar (the rays inserted as sources)."""
+        N, R = p.shape[0], rays.shape[0]
+        _check_tensor(p, "p", (N, self.dim))
+        _check_tensor(w, "w", self._chan_shape(w, N))
+        _check_tensor(rays, "rays", (R, 8))
+        _check_tensor(ybar, "ybar", self._chan_shape(w, R))
+        wbar = torch.empty(self._chan_shape(w, N), device=p.device, dtype=torch.float32) if need_w else None
+        pbar = torch.empty(N, self.dim, device=p.device, dtype=torch.float32) if need_p else None
+        self._serial += 1
+        capi.ray_backward(self._h, self._stream(), _ptr(p), _ptr(w), N, _ptr(rays), R, _ptr(ybar), _ptr(wbar),
+                          _ptr(pbar))
+        return wbar, pbar
+
+
+class FC2T2RayFunction(torch.autograd.Function):
+    """y = integrals of f(.; p, w) along fixed rays, with the adjoints of Sec. 4 (ray2M)."""
+
+    @staticmethod
+    def forward(ctx, p, w, rays, plan: "Plan"):
+        p, w, rays = p.contiguous(), w.contiguous(), rays.contiguous()
+        ctx.plan = plan
+        ctx.save_for_backward(p, w, rays)
+        return plan.ray_forward(p, w, rays)
+
+    @staticmethod
+    def backward(ctx, ybar):
+        p, w, rays = ctx.saved_tensors
+        need_p, need_w = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        wbar = pbar = None
+        if need_p or need_w:
+            wbar, pbar = ctx.plan.ray_backward(p, w, rays, ybar.contiguous(), need_w=need_w, need_p=need_p)
+        return pbar, wbar, None, None
+
+
+def fc2t2_rays(p: torch.Tensor, w: torch.Tensor, rays: torch.Tensor, plan: "Plan") -> torch.Tensor:
+    """Differentiable ray integrals of the transform (Sec. 4)."""
+    return FC2T2RayFunction.apply(p, w, rays, plan)
+
 
 class FC2T2Function(torch.autograd.Function):
     """y = f(q; p, w) with hand-written adjoints (Sec. 4.1); the query gradient is computed when

@@ -141,6 +141,26 @@ def pinhole_ray_samples(rng, width: int, height: int, samples: int) -> np.ndarra
     return np.clip(pts.reshape(-1, 3), 0.0, np.nextafter(1.0, 0.0))
 
 
+def pinhole_rays(width: int, height: int) -> np.ndarray:
+    """Ray records [width * height, 8] (origin, direction, t_in, t_out) of the pixel-centre rays of
+    the same pinhole camera as ``pinhole_ray_samples``: the ray through pixel (i, j) aims at the point
+    ((i + 0.5) / width, (j + 0.5) / height, 0) of the cube's z = 0 face, and [t_in, t_out] is its
+    slab intersection with the unit cube (float32)."""
+    o = np.array([0.5, 0.5, -1.0])
+    u = (np.arange(width) + 0.5) / width
+    v = (np.arange(height) + 0.5) / height
+    uu, vv = np.meshgrid(u, v, indexing="xy")
+    d = np.stack([uu.ravel() - 0.5, vv.ravel() - 0.5, np.ones(uu.size)], axis=1)
+    with np.errstate(divide="ignore"):
+        inv = 1.0 / d
+    t0 = (0.0 - o) * inv
+    t1 = (1.0 - o) * inv
+    t_in = np.max(np.minimum(t0, t1), axis=1)
+    t_out = np.min(np.maximum(t0, t1), axis=1)
+    out = np.concatenate([np.broadcast_to(o, d.shape), d, t_in[:, None], t_out[:, None]], axis=1)
+    return _f32(out)
+
+
 def sphere_rays(N: int = 1 << 18, width: int = 512, height: int = 512, samples: int = 128,
                 grid: int = 64, order: int = 8, sigma: float = 0.01, seed: int = 3) -> Workload:
     """3D ray-query workload: sphere-surface sources, pinhole-ray stratified queries."""
