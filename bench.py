@@ -43,7 +43,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) of one transform's M2L launches, from an ncu capture of the current
 # kernel builds (profiles/k_m2l_sep_uniform3d.md, profiles/k_m2l_tc_bf16x3_uniform3d.md); None
 # where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"separable": None,
+M2L_TRAFFIC_BYTES = {"separable": (88.1 + 12.6 + 222.3 + 63.5 + 222.4 + 63.5 + 161.8 + 5.0 + 176.4 + 16.7 + 62.2 + 1.2) * 1e6,
                      "bf16x3": (464.0 + 82.8) * 1e6}
 
 
