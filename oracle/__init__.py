@@ -19,6 +19,7 @@ Public functions (all arrays are numpy, float64 unless stated):
     series along rays (Sec. 4, integral-implicit layer) and their adjoint (w̄, p̄).
 * ``direct(desc, p, w, q, sel=None)`` -> exact O(NM) sum of Eq. 1.
 * ``kernel_derivs(desc, c)`` -> d^m psi(c), |m| <= order, graded order.
+* ``fit_coeffs(desc, c, h)`` -> the least-squares fitted replacements of d^m psi(c) (``fit=True``).
 * ``multi_indices(dim, order)`` -> exponents [P, dim], graded order.
 * ``bin_cells(desc, x)`` -> finest-level linear cell index per point (FP32 rule).
 
@@ -78,6 +79,7 @@ class _Desc(ctypes.Structure):
         ("n_poly", ctypes.c_int),
         ("lo", ctypes.c_double),
         ("hi", ctypes.c_double),
+        ("fit", ctypes.c_int),
     ]
 
 
@@ -93,6 +95,8 @@ def _load():
             lib.orc_multi_indices.restype = ctypes.c_int
             lib.orc_kernel_derivs.argtypes = [ctypes.POINTER(_Desc), P, P]
             lib.orc_kernel_derivs.restype = ctypes.c_int
+            lib.orc_fit_coeffs.argtypes = [ctypes.POINTER(_Desc), P, ctypes.c_double, P]
+            lib.orc_fit_coeffs.restype = ctypes.c_int
             lib.orc_bin.argtypes = [ctypes.POINTER(_Desc), P, ctypes.c_int64, P]
             lib.orc_bin.restype = ctypes.c_int
             lib.orc_transform.argtypes = [ctypes.POINTER(_Desc),
@@ -131,6 +135,7 @@ class OracleDesc:
     poly_coef: Optional[Sequence[float]] = None
     lo: float = 0.0
     hi: float = 1.0
+    fit: bool = False                 # least-squares fitted M2L coefficients (Sec. 3.1)
     _keep: list = field(default_factory=list, repr=False)
 
     def c(self) -> _Desc:
@@ -147,6 +152,7 @@ class OracleDesc:
             d.poly_coef = None
             d.n_poly = 0
         d.lo, d.hi = float(self.lo), float(self.hi)
+        d.fit = 1 if self.fit else 0
         return d
 
 
@@ -177,6 +183,16 @@ def kernel_derivs(desc: OracleDesc, c) -> np.ndarray:
     out = np.zeros(num_coeffs(desc.dim, desc.order), dtype=np.float64)
     cd = desc.c()
     _load().orc_kernel_derivs(ctypes.byref(cd), c.ctypes.data, out.ctypes.data)
+    return out
+
+
+def fit_coeffs(desc: OracleDesc, c, h: float) -> np.ndarray:
+    """The least-squares fitted coefficients a_m (|m| <= order, graded) that replace d^m psi(c) in
+    M2L for cells of width h (Sec. 3.1; the fit is over the separations c + [-h, h]^dim)."""
+    c = _f64(c, (desc.dim,))
+    out = np.zeros(num_coeffs(desc.dim, desc.order), dtype=np.float64)
+    cd = desc.c()
+    _load().orc_fit_coeffs(ctypes.byref(cd), c.ctypes.data, float(h), out.ctypes.data)
     return out
 
 

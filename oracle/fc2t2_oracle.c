@@ -67,6 +67,7 @@ typedef struct {
     const double *poly_coef; /* polynomial coefficients in graded order */
     int n_poly;              /* number of polynomial coefficients */
     double lo, hi;           /* domain [lo, hi)^dim */
+    int fit;                 /* 0: Taylor coefficients in M2L; 1: least-squares fitted ones */
 } orc_desc;
 
 /* deliberate-mistake switches, used only by the pin-sensitivity tests */
@@ -280,6 +281,120 @@ static double kernel_value(const orc_desc *d, const double *x) {
     }
     free(pex);
     return acc;
+}
+
+
+/* ------------------------------------------------------- fitted operators
+ * Sec. 3.1 replaces the Taylor coefficients of the kernel about a cell-pair offset c by those of
+ * a polynomial fitted to the kernel in the least-squares sense over the separations the pair can
+ * have.  Reading taken here: with x = h xi, the separation of a source and a target in cells of
+ * width h whose centres are c apart ranges over c + [-h, h]^D, and the coefficients b_m (|m| <= rho)
+ * of sum_m b_m xi^m / m! minimise sum_j w_j (psi(c + h xi_j) - sum_m b_m xi_j^m / m!)^2 over the
+ * tensor Gauss-Legendre grid of rho + 2 points per dimension on [-1, 1]^D (weights w_j).  The
+ * derivative of order m is then replaced by a_m = b_m / h^|m|. */
+typedef struct { int npts, P, D; double *xi, *w, *phi, *chol; } orc_lsq;
+
+/* Gauss-Legendre points and weights of K nodes on [-1, 1]: Newton's method on the Legendre
+ * three-term recurrence */
+static void legendre_nodes(int K, double *x, double *w) {
+    for (int i = 0; i < K; ++i) {
+        double z = cos(3.14159265358979323846 * (i + 0.75) / (K + 0.5)), dp = 1.0;
+        for (int it = 0; it < 200; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int m = 2; m <= K; ++m) {
+                const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = K * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-15) break;
+        }
+        x[i] = z;
+        w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+static void lsq_init(orc_lsq *f, const orc_index *ix, int D, int rho) {
+    const int K = rho + 2, P = ix->P;
+    double x[ORC_MAXRHO + 2], w[ORC_MAXRHO + 2];
+    legendre_nodes(K, x, w);
+    int npts = 1;
+    for (int i = 0; i < D; ++i) npts *= K;
+    f->npts = npts; f->P = P; f->D = D;
+    f->xi = (double *)malloc(sizeof(double) * npts * D);
+    f->w = (double *)malloc(sizeof(double) * npts);
+    f->phi = (double *)malloc(sizeof(double) * npts * P);
+    f->chol = (double *)calloc((size_t)P * P, sizeof(double));
+    for (int j = 0; j < npts; ++j) {
+        int r = j;
+        double pw[ORC_MAXD][ORC_MAXRHO + 1];
+        f->w[j] = 1.0;
+        for (int i = 0; i < D; ++i) {
+            const int k = r % K;
+            r /= K;
+            f->xi[j * D + i] = x[k];
+            f->w[j] *= w[k];
+            powers_over_fact(x[k], rho, pw[i]);
+        }
+        for (int m = 0; m < P; ++m) f->phi[(size_t)j * P + m] = mono(ix, m, pw);
+    }
+    /* Gram matrix G = sum_j w_j phi_j phi_j^T, then its Cholesky factor (lower, in place) */
+    double *G = f->chol;
+    for (int j = 0; j < npts; ++j)
+        for (int m = 0; m < P; ++m)
+            for (int n2 = 0; n2 <= m; ++n2) G[m * P + n2] += f->w[j] * f->phi[(size_t)j * P + m] * f->phi[(size_t)j * P + n2];
+    for (int m = 0; m < P; ++m) {
+        for (int n2 = 0; n2 < m; ++n2) {
+            double acc = G[m * P + n2];
+            for (int k = 0; k < n2; ++k) acc -= G[m * P + k] * G[n2 * P + k];
+            G[m * P + n2] = acc / G[n2 * P + n2];
+        }
+        double acc = G[m * P + m];
+        for (int k = 0; k < m; ++k) acc -= G[m * P + k] * G[m * P + k];
+        G[m * P + m] = sqrt(acc);
+    }
+}
+
+static void lsq_free(orc_lsq *f) { free(f->xi); free(f->w); free(f->phi); free(f->chol); }
+
+/* the fitted coefficients a_m (in place of d^m psi(c)) for offset c and cell width h */
+static void lsq_fit(const orc_lsq *f, const orc_desc *d, const orc_index *ix, const double *c, double h,
+                    double *out) {
+    const int P = f->P, D = f->D;
+    double *b = (double *)calloc((size_t)P, sizeof(double));
+    for (int j = 0; j < f->npts; ++j) {
+        double xx[ORC_MAXD];
+        for (int i = 0; i < D; ++i) xx[i] = c[i] + h * f->xi[j * D + i];
+        const double v = f->w[j] * kernel_value(d, xx);
+        for (int m = 0; m < P; ++m) b[m] += v * f->phi[(size_t)j * P + m];
+    }
+    const double *Lc = f->chol;
+    for (int m = 0; m < P; ++m) {          /* forward substitution */
+        double acc = b[m];
+        for (int k = 0; k < m; ++k) acc -= Lc[m * P + k] * b[k];
+        b[m] = acc / Lc[m * P + m];
+    }
+    for (int m = P - 1; m >= 0; --m) {     /* back substitution with the transpose */
+        double acc = b[m];
+        for (int k = m + 1; k < P; ++k) acc -= Lc[k * P + m] * b[k];
+        b[m] = acc / Lc[m * P + m];
+    }
+    for (int m = 0; m < P; ++m) out[m] = b[m] / pow(h, ix->deg[m]);
+    free(b);
+}
+
+/* exported for the tests: the fitted coefficients at offset c, cell width h */
+int orc_fit_coeffs(const orc_desc *d, const double *c, double h, double *out) {
+    orc_index ix;
+    index_init(&ix, d->dim, d->order);
+    orc_lsq f;
+    lsq_init(&f, &ix, d->dim, d->order);
+    lsq_fit(&f, d, &ix, c, h, out);
+    lsq_free(&f);
+    index_free(&ix);
+    return ix.P;
 }
 
 /* ----------------------------------------------------------------- binning */
@@ -596,6 +711,8 @@ static int pipeline(const orc_desc *d,
     int nb = 1;
     for (int i = 0; i < D; ++i) nb *= 7;
     double *dtab = (double *)malloc(sizeof(double) * nb * P);
+    orc_lsq lsq;
+    if (d->fit) lsq_init(&lsq, &ix, D, rho);
     /* for every k: the n with |n| <= rho - |k| and the graded index of n + k */
     int *pstart = (int *)malloc(sizeof(int) * (P + 1));
     int *pn = (int *)malloc(sizeof(int) * P * P), *pnk = (int *)malloc(sizeof(int) * P * P);
@@ -622,7 +739,8 @@ static int pipeline(const orc_desc *d,
             double c[ORC_MAXD];
             for (int k = 0; k < D; ++k) { oo[k] = r % 7 - 3; r /= 7; c[k] = oo[k] * h; }
             if (fault == ORC_FAULT_TRANSPOSE) for (int k = 0; k < D; ++k) c[k] = -c[k];
-            kernel_derivs_ix(d, &ix, c, dtab + (size_t)o * P);
+            if (d->fit) lsq_fit(&lsq, d, &ix, c, h, dtab + (size_t)o * P);
+            else kernel_derivs_ix(d, &ix, c, dtab + (size_t)o * P);
         }
         int64_t Gl = G[l];
         #pragma omp parallel for schedule(dynamic, 64)
@@ -655,6 +773,7 @@ static int pipeline(const orc_desc *d,
         }
     }
     free(dtab); free(pstart); free(pn); free(pnk);
+    if (d->fit) lsq_free(&lsq);
 
     /* ---- L2L: script-L(n, q') += sum_{k >= n} d'^(k-n)/(k-n)! script-L(k, q''), coarse to fine */
     if (fault != ORC_FAULT_NO_L2L) {

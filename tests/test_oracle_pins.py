@@ -573,3 +573,66 @@ def test_ray_source_gradient_vs_central_differences():
             pm[n, k] -= eps
             fd = (ybar @ oracle.ray_forward(d, pp, w, rays) - ybar @ oracle.ray_forward(d, pm, w, rays)) / (2 * eps)
             assert abs(fd - pbar[n, k]) <= 1e-6 * (np.abs(pbar).max() + 1e-30), (n, k, fd, pbar[n, k])
+
+
+# ---------------------------------------------------------------- fitted operators (Sec. 3.1)
+
+@pytest.mark.parametrize("name", ["r2", "one_minus_r2_sq", "odd_mixed"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_fitted_operators_exact_for_polynomial_kernels(name, dim):
+    """A least-squares fit reproduces a polynomial of degree <= rho exactly, so the fitted
+    coefficients equal the kernel's derivatives and the fitted transform equals the Taylor one."""
+    terms = {m: v for m, v in POLYS_3D[name].items() if dim == 3 or m[2] == 0}
+    deg = max(sum(m) for m in terms)
+    coef = poly_coef(terms, dim, deg)
+    order = max(deg, 4)
+    d_fit = oracle.OracleDesc(dim=dim, grid=8, order=order, kernel="poly", poly_coef=coef, fit=True)
+    d_tay = oracle.OracleDesc(dim=dim, grid=8, order=order, kernel="poly", poly_coef=coef)
+    c = np.array([0.25, -0.125, 0.375][:dim])
+    h = 0.125
+    a, t = oracle.fit_coeffs(d_fit, c, h), oracle.kernel_derivs(d_tay, c)
+    hm = np.array([h ** sum(m) for m in graded(dim, order)])   # compared in the scaled form h^|m| a_m
+    assert np.max(np.abs((a - t) * hm)) <= 1e-11 * max(1.0, np.abs(t * hm).max())
+    p, w, q = small_inputs(180 + dim, dim, 50, 40)
+    y_fit, y_tay = oracle.forward(d_fit, p, w, q), oracle.forward(d_tay, p, w, q)
+    assert np.max(np.abs(y_fit - y_tay)) <= 1e-9 * max(1.0, np.abs(y_tay).max())
+
+
+@pytest.mark.parametrize("dim,order", [(2, 5), (3, 4), (3, 6)])
+def test_fitted_operators_solve_the_least_squares_problem(dim, order):
+    """The fitted coefficients are the weighted least-squares solution on the tensor
+    Gauss-Legendre grid of order + 2 points per dimension over c + [-h, h]^dim: they agree with
+    numpy's lstsq on that grid (nodes from numpy), and the residual is orthogonal to the basis."""
+    import math
+    sigma, h = 0.08, 0.125
+    d = oracle.OracleDesc(dim=dim, grid=8, order=order, sigma=sigma, fit=True)
+    c = np.array([0.25, 0.125, -0.375][:dim])
+    a = oracle.fit_coeffs(d, c, h)
+    K = order + 2
+    x1, w1 = np.polynomial.legendre.leggauss(K)
+    grids = np.meshgrid(*([x1] * dim), indexing="ij")
+    xi = np.stack([g.ravel() for g in grids], axis=1)
+    wts = np.prod(np.stack(np.meshgrid(*([w1] * dim), indexing="ij"), axis=-1).reshape(-1, dim), axis=1)
+    mis = graded(dim, order)
+    basis = np.stack([np.prod([xi[:, k] ** m[k] / math.factorial(m[k]) for k in range(dim)], axis=0)
+                      for m in mis], axis=1)
+    f = np.exp(-np.sum((c[None, :] + h * xi) ** 2, axis=1) / (2 * sigma ** 2))
+    sw = np.sqrt(wts)
+    b_ref = np.linalg.lstsq(basis * sw[:, None], f * sw, rcond=None)[0]
+    b = a * np.array([h ** sum(m) for m in mis])
+    assert np.max(np.abs(b - b_ref)) <= 1e-8 * np.abs(b_ref).max()
+    resid = f - basis @ b
+    assert np.max(np.abs(basis.T @ (wts * resid))) <= 1e-10 * np.abs(f).max()
+
+
+def test_fitted_operators_reduce_the_error_of_coarse_grids():
+    """With cells wider than the kernel (h / sigma 1.25-1.6) the fitted operators bring the
+    transform closer to the exact sum than the Taylor coefficients at the same order (the paper's
+    reason for the fit, Sec. 3.1)."""
+    p, w, q = small_inputs(190, 3, 300, 250)
+    for sigma, order in ((0.08, 4), (0.1, 4), (0.08, 6)):
+        errs = []
+        for fit in (False, True):
+            d = oracle.OracleDesc(dim=3, grid=8, order=order, sigma=sigma, fit=fit)
+            errs.append(rel(oracle.forward(d, p, w, q), oracle.direct(d, p, w, q)))
+        assert errs[1] < 0.6 * errs[0], (sigma, order, errs)
