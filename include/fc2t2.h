@@ -106,6 +106,14 @@ typedef struct {
     int check_domain;            /* nonzero: reject points outside the domain (synchronises) */
     int64_t max_sources;         /* workspace bound on N (>= 0) */
     int64_t max_queries;         /* workspace bound on M (>= 0) */
+    int fit;                     /* 0: M2L uses the kernel's Taylor coefficients about each cell-pair
+                                    offset c (Sec. 3).  1: least-squares fitted ones (Sec. 3.1): the
+                                    polynomial of total degree `order` closest to psi over the pair's
+                                    separations c + [-h, h]^dim in the discrete L2 norm of the tensor
+                                    Gauss-Legendre grid of order + 2 points per dimension (more
+                                    accurate when cells are wide next to the kernel).  Not with the
+                                    SEPARABLE M2L (UNSUPPORTED): the fit does not factor per
+                                    dimension. */
 } fc2t2_plan_desc;
 
 /* Build a plan: validate `desc`, build the M2L / M2M / L2L operator tables in FP64 on

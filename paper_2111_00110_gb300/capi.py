@@ -71,6 +71,7 @@ class PlanDesc(ctypes.Structure):
         ("check_domain", ctypes.c_int),
         ("max_sources", ctypes.c_int64),
         ("max_queries", ctypes.c_int64),
+        ("fit", ctypes.c_int),
     ]
 
 

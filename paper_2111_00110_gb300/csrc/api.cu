@@ -1,6 +1,7 @@
 // C ABI of the FC2T2 library: plan creation (operator tables, workspace) and the
 // forward / backward pipelines (Sec. 3 and Sec. 4.1 of arXiv 2111.00110).
 #include <cmath>
+#include <memory>
 #include <cstdio>
 #include <cstring>
 #include <string>
@@ -61,6 +62,122 @@ static void gaussian_scaled_derivs_1d(double sigma, double h, double x, int J, d
         f *= r;
     }
 }
+
+// psi(x) on the host (Gaussian or polynomial)
+static double kernel_value_host(const fc2t2_plan_s *pl, const double *x) {
+    const int D = pl->D;
+    if (pl->desc.kernel == FC2T2_KERNEL_GAUSSIAN) {
+        double r2 = 0.0;
+        for (int d = 0; d < D; ++d) r2 += x[d] * x[d];
+        return std::exp(-r2 / (2.0 * pl->desc.sigma * pl->desc.sigma));
+    }
+    int pdeg = 0;
+    while (ncoef(D, pdeg) < (int)pl->poly.size()) ++pdeg;
+    HostIndex px(D, pdeg);
+    double acc = 0.0;
+    for (int a = 0; a < (int)pl->poly.size(); ++a) {
+        double term = pl->poly[a];
+        for (int d = 0; d < D && term != 0.0; ++d)
+            for (int t = 0; t < px.e[3 * a + d]; ++t) term *= x[d];
+        acc += term;
+    }
+    return acc;
+}
+
+// Least-squares operators (Sec. 3.1: the Taylor coefficients of the kernel about a cell-pair
+// offset c replaced by those of a polynomial fitted to the kernel over the pair's separations).
+// With x = h xi, the separations of a source and a target in cells of width h whose centres are c
+// apart are c + [-h, h]^D; the scaled coefficients b_m (|m| <= rho) of sum_m b_m xi^m / m! minimise
+// sum_j w_j (psi(c + h xi_j) - sum_m b_m xi_j^m / m!)^2 over the tensor Gauss-Legendre grid of
+// rho + 2 points per dimension on [-1, 1]^D.  b_m takes the place of Dt[m] = h^|m| d^m psi(c).  The
+// Gram matrix depends only on the grid: it is factored once (Cholesky) and each offset solves
+// against its own right-hand side.
+struct LsqFit {
+    int D = 0, P = 0, npts = 0;
+    std::vector<double> xi, w, phi, chol;   // points [npts][D], weights, basis [npts][P], factor [P][P]
+
+    LsqFit(const fc2t2_plan_s *pl, const HostIndex &ix) : D(pl->D), P(ix.P) {
+        const int K = pl->rho + 2;
+        std::vector<double> x(K), wk(K);
+        for (int i = 0; i < K; ++i) {   // Legendre P_K roots by Newton's method on the recurrence
+            double z = std::cos(M_PI * (i + 0.75) / (K + 0.5)), dp = 1.0;
+            for (int it = 0; it < 200; ++it) {
+                double p0 = 1.0, p1 = z;
+                for (int m = 2; m <= K; ++m) {
+                    const double p2 = ((2.0 * m - 1.0) * z * p1 - (m - 1.0) * p0) / m;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                dp = K * (z * p1 - p0) / (z * z - 1.0);
+                const double dz = p1 / dp;
+                z -= dz;
+                if (std::fabs(dz) < 1e-15) break;
+            }
+            x[i] = z;
+            wk[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+        }
+        npts = 1;
+        for (int d = 0; d < D; ++d) npts *= K;
+        xi.resize((size_t)npts * D);
+        w.resize(npts);
+        phi.resize((size_t)npts * P);
+        for (int j = 0; j < npts; ++j) {
+            int r = j;
+            double pw[3][kMaxOrder + 1];
+            w[j] = 1.0;
+            for (int d = 0; d < D; ++d) {
+                const int k = r % K;
+                r /= K;
+                xi[(size_t)j * D + d] = x[k];
+                w[j] *= wk[k];
+                pw[d][0] = 1.0;
+                for (int t = 1; t <= pl->rho; ++t) pw[d][t] = pw[d][t - 1] * x[k] / t;
+            }
+            for (int m = 0; m < P; ++m) {
+                double v = 1.0;
+                for (int d = 0; d < D; ++d) v *= pw[d][ix.e[3 * m + d]];
+                phi[(size_t)j * P + m] = v;
+            }
+        }
+        chol.assign((size_t)P * P, 0.0);
+        for (int j = 0; j < npts; ++j)
+            for (int m = 0; m < P; ++m) {
+                const double a = w[j] * phi[(size_t)j * P + m];
+                for (int n = 0; n <= m; ++n) chol[(size_t)m * P + n] += a * phi[(size_t)j * P + n];
+            }
+        for (int m = 0; m < P; ++m) {
+            for (int n = 0; n < m; ++n) {
+                double acc = chol[(size_t)m * P + n];
+                for (int k = 0; k < n; ++k) acc -= chol[(size_t)m * P + k] * chol[(size_t)n * P + k];
+                chol[(size_t)m * P + n] = acc / chol[(size_t)n * P + n];
+            }
+            double acc = chol[(size_t)m * P + m];
+            for (int k = 0; k < m; ++k) acc -= chol[(size_t)m * P + k] * chol[(size_t)m * P + k];
+            chol[(size_t)m * P + m] = std::sqrt(acc);
+        }
+    }
+
+    void scaled(const fc2t2_plan_s *pl, const double *c, double h, double *out) const {
+        std::vector<double> b(P, 0.0);
+        for (int j = 0; j < npts; ++j) {
+            double x[3] = {0.0, 0.0, 0.0};
+            for (int d = 0; d < D; ++d) x[d] = c[d] + h * xi[(size_t)j * D + d];
+            const double v = w[j] * kernel_value_host(pl, x);
+            for (int m = 0; m < P; ++m) b[m] += v * phi[(size_t)j * P + m];
+        }
+        for (int m = 0; m < P; ++m) {
+            double acc = b[m];
+            for (int k = 0; k < m; ++k) acc -= chol[(size_t)m * P + k] * b[k];
+            b[m] = acc / chol[(size_t)m * P + m];
+        }
+        for (int m = P - 1; m >= 0; --m) {
+            double acc = b[m];
+            for (int k = m + 1; k < P; ++k) acc -= chol[(size_t)k * P + m] * b[k];
+            b[m] = acc / chol[(size_t)m * P + m];
+        }
+        for (int m = 0; m < P; ++m) out[m] = b[m];
+    }
+};
 
 // Dt[m] = h^|m| d^m psi(c) for every graded m.
 static void scaled_derivs(const fc2t2_plan_s *pl, const HostIndex &ix, const double *c, double h,
@@ -168,13 +285,16 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
     std::vector<float> dtab((size_t)pl->nlev * nofs * Pp, 0.0f);
     std::vector<double> dtab64((size_t)pl->nlev * nofs * P, 0.0);
     std::vector<double> tmp(P);
+    std::unique_ptr<LsqFit> fit;
+    if (pl->desc.fit) fit.reset(new LsqFit(pl, ix));
     for (int l = 0; l < pl->nlev; ++l) {
         const double h = pl->lev[l].h;
         for (int o = 0; o < nofs; ++o) {
             double c[3] = {0, 0, 0};
             int r = o;
             for (int d = 0; d < D; ++d) { c[d] = (double)(r % 7 - 3) * h; r /= 7; }
-            scaled_derivs(pl, ix, c, h, tmp.data());
+            if (fit) fit->scaled(pl, c, h, tmp.data());
+            else scaled_derivs(pl, ix, c, h, tmp.data());
             for (int k = 0; k < P; ++k) {
                 dtab[((size_t)l * nofs + o) * Pp + k] = (float)tmp[k];
                 dtab64[((size_t)l * nofs + o) * P + k] = tmp[k];
@@ -278,6 +398,9 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
         return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
     if (d->m2l == FC2T2_M2L_SEPARABLE && (d->kernel != FC2T2_KERNEL_GAUSSIAN || d->dim != 3))
         return set_error(FC2T2_ERR_UNSUPPORTED, "the separable M2L needs the Gaussian kernel and dim = 3");
+    if (d->fit != 0 && d->fit != 1) return set_error(FC2T2_ERR_INVALID_ARG, "fit must be 0 or 1");
+    if (d->fit && d->m2l == FC2T2_M2L_SEPARABLE)
+        return set_error(FC2T2_ERR_UNSUPPORTED, "fitted operators do not factor per dimension (no separable M2L)");
     if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||
         d->max_queries > (int64_t)INT32_MAX)
         return set_error(FC2T2_ERR_INVALID_ARG, "max_sources / max_queries out of range");

@@ -121,8 +121,8 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
         return set_error(FC2T2_ERR_INVALID_ARG, "sigma must be positive");
     if (!(desc->hi > desc->lo) || !std::isfinite(desc->lo) || !std::isfinite(desc->hi))
         return set_error(FC2T2_ERR_INVALID_ARG, "domain must satisfy lo < hi");
-    if (desc->channels != 1 || desc->m2l != FC2T2_M2L_FP32)
-        return set_error(FC2T2_ERR_UNSUPPORTED, "the allocation-free path supports one channel, FP32 M2L");
+    if (desc->channels != 1 || desc->m2l != FC2T2_M2L_FP32 || desc->fit != 0)
+        return set_error(FC2T2_ERR_UNSUPPORTED, "the allocation-free path supports one channel, FP32 M2L, Taylor operators");
     if (desc->grid < 4 || (desc->grid & (desc->grid - 1)))
         return set_error(FC2T2_ERR_INVALID_ARG, "grid must be a power of two >= 4");
     int64_t cells = 1;

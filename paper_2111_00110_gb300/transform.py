@@ -41,7 +41,8 @@ class Plan:
     def __init__(self, dim: int, grid: int, order: int, sigma: float = 0.05, *,
                  kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
                  lo: float = 0.0, hi: float = 1.0, m2l: str = "fp32", check_domain: bool = False,
-                 max_sources: int = 1 << 20, max_queries: int = 1 << 20, channels: int = 1, device=None):
+                 max_sources: int = 1 << 20, max_queries: int = 1 << 20, channels: int = 1, fit: bool = False,
+                 device=None):
         self.dim, self.grid, self.order, self.channels = dim, grid, order, int(channels)
         self._serial = 0   # counts the calls that replace the plan's expansion
         self.sigma, self.kernel, self.lo, self.hi, self.m2l = sigma, kernel, lo, hi, m2l
@@ -60,6 +61,7 @@ class Plan:
         d.channels = self.channels
         d.m2l = capi.M2L_PREC[m2l]
         d.check_domain = 1 if check_domain else 0
+        d.fit = 1 if fit else 0   # least-squares fitted M2L operators (Sec. 3.1)
         d.max_sources, d.max_queries = self.max_sources, self.max_queries
         with torch.cuda.device(self.device):
             self._h = capi.plan_create(d)

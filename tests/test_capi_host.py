@@ -55,7 +55,7 @@ def _desc(**kw):
 @pytest.mark.parametrize("field,value,status", [
     ("dim", 4, 1), ("dim", 1, 1), ("grid", 12, 1), ("grid", 2, 1), ("grid", 2048, 1),
     ("order", 0, 1), ("order", 9, 1), ("sigma", 0.0, 1), ("sigma", -1.0, 1),
-    ("hi", 0.0, 1), ("channels", 0, 1), ("channels", 4097, 1), ("m2l", 7, 2), ("max_sources", -1, 1), ("kernel", 5, 1),
+    ("hi", 0.0, 1), ("channels", 0, 1), ("channels", 4097, 1), ("m2l", 7, 2), ("fit", 2, 1), ("max_sources", -1, 1), ("kernel", 5, 1),
 ])
 def test_bad_descriptors_are_rejected_on_the_host(lib, field, value, status):
     out = ctypes.c_void_p(123)
@@ -93,3 +93,9 @@ def test_null_arguments(lib):
     assert lib.fc2t2_expand(None, None, None, None, 0) == 1
     assert lib.fc2t2_evaluate(None, None, None, 0, 0, None) == 1
     assert lib.fc2t2_evaluate_grid(None, None, None, None, 0, None) == 1
+
+
+def test_fitted_operators_exclude_the_separable_m2l(lib):
+    out = ctypes.c_void_p(123)
+    assert lib.fc2t2_plan_create(ctypes.byref(_desc(m2l=5, fit=1)), ctypes.byref(out)) == 2
+    assert out.value is None

@@ -412,3 +412,30 @@ def test_l2p_without_finest_l2l_matches_l2l(lib, dim, order, m2l):
     assert_close(wbar.cpu().numpy(), wo, rel=bar[0], elem=bar[1], what="wbar from levels")
     assert_close(pbar.cpu().numpy(), po, rel=bar[0], elem=bar[1], what="pbar from levels")
     assert rel_l2(qb_few.cpu().numpy(), qb_many[:few].cpu().numpy()) <= 1e-5
+
+
+# ------------------------------------------------------- least-squares fitted operators
+
+@pytest.mark.parametrize("dim,grid,order,m2l", [(3, 8, 4, "fp32"), (3, 16, 6, "bf16x3"), (3, 16, 5, "tf32x3"),
+                                                (2, 16, 4, "fp32"), (3, 8, 6, "tf32")])
+def test_fitted_operators(lib, dim, grid, order, m2l):
+    """M2L with least-squares fitted coefficients (Sec. 3.1) against the oracle's own fit, forward
+    and backward; with cells wider than the kernel the fitted transform is closer to the exact sum
+    than the Taylor one."""
+    sigma = 0.8 / grid                  # h / sigma = 1.25
+    wl = workloads.uniform(990 + dim + order, dim, 2500, 2000, grid, order, sigma)
+    ybar = wl.ybar()
+    plan = make_plan(dim, grid, order, sigma, wl.N, wl.M, m2l=m2l, fit=True)
+    y = run_forward(plan, wl.p, wl.w, wl.q)
+    wbar, pbar = run_backward(plan, wl.p, wl.w, wl.q, ybar)
+    d = odesc(dim, grid, order, sigma, fit=True)
+    yo = oracle.forward(d, *f64(wl.p, wl.w, wl.q))
+    wo, po = oracle.backward(d, *f64(wl.p, wl.w, wl.q, ybar))
+    bar = TC_BARS[m2l] if m2l in TC_BARS else (REL_L2, ELEM)
+    assert_close(y, yo, rel=bar[0], elem=bar[1], what=f"fitted forward ({m2l})")
+    assert_close(wbar, wo, rel=bar[0], elem=bar[1], what=f"fitted wbar ({m2l})")
+    assert_close(pbar, po, rel=bar[0], elem=bar[1], what=f"fitted pbar ({m2l})")
+    if m2l == "fp32":
+        exact = oracle.direct(d, *f64(wl.p, wl.w, wl.q))
+        taylor = run_forward(make_plan(dim, grid, order, sigma, wl.N, wl.M), wl.p, wl.w, wl.q)
+        assert rel_l2(y, exact) < 0.6 * rel_l2(taylor, exact)
