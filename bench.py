@@ -164,20 +164,24 @@ def cpu_oracle_step(wl, sel_q, sel_p):
     return time.perf_counter() - t0
 
 
-def oracle_reference_sample(wl, n=4096, seed=12345):
+def oracle_reference_sample(wl, n=4096, seed=12345, fit=False, exact=None):
     """Oracle y at n seeded queries, and (wbar, pbar) at n seeded sources for the seeded
-    cotangent wl.ybar() -- the accuracy reference for every M2L form."""
+    cotangent wl.ybar() -- the accuracy reference for every M2L form (``fit``: with the
+    least-squares fitted operators); ``exact``: the direct sum at the same queries, computed once
+    (the truncation error of each form is measured against it)."""
     import numpy as np
     import oracle
     oracle.build()
     rng = np.random.default_rng(seed)
     sq = np.sort(rng.choice(wl.M, size=n, replace=False))
     sp = np.sort(rng.choice(wl.N, size=n, replace=False))
-    d = oracle.OracleDesc(dim=3, grid=wl.grid, order=wl.order, sigma=wl.sigma)
+    d = oracle.OracleDesc(dim=3, grid=wl.grid, order=wl.order, sigma=wl.sigma, fit=fit)
     p, w, q = (np.asarray(a, dtype=np.float64) for a in (wl.p, wl.w, wl.q))
     y = oracle.forward(d, p, w, q, sel=sq)
     wb, pb = oracle.backward(d, p, w, q, np.asarray(wl.ybar(), dtype=np.float64), sel=sp)
-    return {"sq": sq, "sp": sp, "y": y, "wbar": wb, "pbar": pb}
+    if exact is None:
+        exact = oracle.direct(d, p, w, q, sel=sq)
+    return {"sq": sq, "sp": sp, "y": y, "wbar": wb, "pbar": pb, "exact": exact}
 
 
 def rel_l2(a, b):
@@ -223,7 +227,7 @@ class Measured:
     pass
 
 
-def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, clocks=False, steps=None):
+def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, clocks=False, steps=None, fit=False):
     """Time `steps` (default `args.steps`) fwd+bwd steps of one M2L form; per-stage device times
     from the library's events on the launching stream; optional end-to-end loop from pinned host
     buffers."""
@@ -231,7 +235,7 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
     import torch
     from paper_2111_00110_gb300.transform import Plan
 
-    plan = Plan(3, wl.grid, wl.order, wl.sigma, m2l=mode, max_sources=wl.N, max_queries=wl.M, device=dev)
+    plan = Plan(3, wl.grid, wl.order, wl.sigma, m2l=mode, max_sources=wl.N, max_queries=wl.M, fit=fit, device=dev)
     p = torch.from_numpy(wl.p).to(dev)
     w = torch.from_numpy(wl.w).to(dev)
     q = torch.from_numpy(wl.q).to(dev)
@@ -252,9 +256,11 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
         y = plan.forward(p, w, q)
         wb, pb = plan.backward(p, w, q, torch.from_numpy(wl.ybar()).to(dev))
         torch.cuda.synchronize(dev)
-        out.err = {"y": rel_l2(y.cpu().numpy()[ref["sq"]], ref["y"]),
+        ys = y.cpu().numpy()[ref["sq"]]
+        out.err = {"y": rel_l2(ys, ref["y"]),
                    "wbar": rel_l2(wb.cpu().numpy()[ref["sp"]], ref["wbar"]),
-                   "pbar": rel_l2(pb.cpu().numpy()[ref["sp"]], ref["pbar"])}
+                   "pbar": rel_l2(pb.cpu().numpy()[ref["sp"]], ref["pbar"]),
+                   "y_vs_exact_sum": rel_l2(ys, ref["exact"])}
     else:
         out.err = None
     for _ in range(max(3, args.warmup)):
@@ -499,6 +505,11 @@ def run_ours(args, rank, world, local_rank):
     if args.m2l == "auto":
         for mode in ("bf16x3", "tf32x3", "tf32", "bf16", "fp32"):
             variants[mode] = measure_mode(mode, wl, args, world, dev, flush, ref=ref, steps=min(args.steps, 10))
+        # the least-squares fitted operators (Sec. 3.1) on the tensor cores, checked against the
+        # oracle's own fit
+        ref_fit = None if ref is None else oracle_reference_sample(wl, fit=True, exact=ref["exact"])
+        variants["bf16x3_fit"] = measure_mode("bf16x3", wl, args, world, dev, flush, ref=ref_fit,
+                                              steps=min(args.steps, 10), fit=True)
     rays = measure_rays(dev, flush, min(args.steps, 10), args.warmup) if (args.m2l == "auto" and rank == 0) else None
     if rank != 0:
         return
