@@ -44,8 +44,12 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
 #pragma unroll
         for (int d = 0; d < D; ++d) z[d] = lo + ((float)cc[d] + 0.5f) * h;
         const int j0 = start[c], j1 = start[c + 1];
+        // each source's record is loaded one iteration ahead (its latency behind the previous
+        // source's arithmetic)
+        float4 rn = j0 < j1 ? __ldg(rec + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int j = j0; j < j1; ++j) {
-            const float4 r = __ldg(rec + j);
+            const float4 r = rn;
+            if (j + 1 < j1) rn = __ldg(rec + j + 1);
             const float xj[3] = {r.x, r.y, r.z};
             float pw[3][RHO + 1];
 #pragma unroll
@@ -146,6 +150,9 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
     const int sc = n < kStageCells ? n : kStageCells;
     const int64_t c0 = (int64_t)blockIdx.x * sc;          // first cell (x0 = c0 mod n, a multiple of sc)
     const int x0 = (int)(c0 % n);
+    // the segment's points, and this thread's first record, are loaded before the rows are staged
+    const int j0 = __ldg(start + c0), j1 = __ldg(start + c0 + sc);
+    float4 rn = j0 + (int)threadIdx.x < j1 ? __ldg(rec + j0 + threadIdx.x) : make_float4(0.f, 0.f, 0.f, 0.f);
     // stage the segment's rows (and its parents' rows)
     {
         const float4 *src0 = reinterpret_cast<const float4 *>(L0 + c0 * Pp);
@@ -165,9 +172,9 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
         }
     }
     __syncthreads();
-    const int j0 = __ldg(start + c0), j1 = __ldg(start + c0 + sc);
     for (int j = j0 + threadIdx.x; j < j1; j += kL2PThreads) {
-        const float4 r = __ldg(rec + j);
+        const float4 r = rn;
+        if (j + kL2PThreads < j1) rn = __ldg(rec + j + kL2PThreads);   // the next record, one round ahead
         const float xj[3] = {r.x, r.y, r.z};
         int cd[3];
 #pragma unroll
