@@ -152,7 +152,12 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
     const int x0 = (int)(c0 % n);
     // the segment's points, and this thread's first record, are loaded before the rows are staged
     const int j0 = __ldg(start + c0), j1 = __ldg(start + c0 + sc);
-    float4 rn = j0 + (int)threadIdx.x < j1 ? __ldg(rec + j0 + threadIdx.x) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+    int in = 0;                                            // and its place in the input order
+    if (j0 + (int)threadIdx.x < j1) {
+        rn = __ldg(rec + j0 + threadIdx.x);
+        in = __ldg(perm + j0 + threadIdx.x);
+    }
     // stage the segment's rows (and its parents' rows)
     {
         const float4 *src0 = reinterpret_cast<const float4 *>(L0 + c0 * Pp);
@@ -174,7 +179,11 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
     __syncthreads();
     for (int j = j0 + threadIdx.x; j < j1; j += kL2PThreads) {
         const float4 r = rn;
-        if (j + kL2PThreads < j1) rn = __ldg(rec + j + kL2PThreads);   // the next record, one round ahead
+        const int i_out = in;
+        if (j + kL2PThreads < j1) {   // the next record, one round ahead
+            rn = __ldg(rec + j + kL2PThreads);
+            in = __ldg(perm + j + kL2PThreads);
+        }
         const float xj[3] = {r.x, r.y, r.z};
         int cd[3];
 #pragma unroll
@@ -222,7 +231,7 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
                 for (int d = 0; d < 3; ++d) g[d] = fmaf(inv_h1 / inv_h0, g1[d], g[d]);
             }
         }
-        l2p_store<D, GRAD>(perm[j], value, g, scale_g, val, grad, accumulate);
+        l2p_store<D, GRAD>(i_out, value, g, scale_g, val, grad, accumulate);
     }
 }
 
