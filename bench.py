@@ -484,6 +484,69 @@ def measure_rays(dev, flush, steps, warmup):
     return out
 
 
+def measure_batched(dev, flush, steps, warmup, n_inst=64):
+    """The batched workload: 64 independent clustered point sets (N_i = M_i log-uniform in
+    [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3) and order (4 or 6) chosen by the
+    autotuner (fastest candidate within 1e-2 rel-L2 of the exact sum, separable M2L).  A step is one
+    batched forward and one batched backward call over all instances (a stream per plan, instances
+    side by side); the same instances run one call after another on one stream for comparison."""
+    import time
+    import torch
+    from paper_2111_00110_gb300 import autotune, workloads
+    from paper_2111_00110_gb300.transform import Plan, backward_batched, forward_batched
+    wls = [workloads.mixture(i) for i in range(n_inst)]
+    ps = [torch.from_numpy(wl.p).to(dev) for wl in wls]
+    ws = [torch.from_numpy(wl.w).to(dev) for wl in wls]
+    qs = [torch.from_numpy(wl.q).to(dev) for wl in wls]
+    t0 = time.time()
+    choices = [autotune.autotune(p, w, q, wl.sigma, target=1e-2, grids=(32, 64), orders=(4, 6),
+                                 m2l=("separable",), sample=512, reps=1)[0]
+               for wl, p, w, q in zip(wls, ps, ws, qs)]
+    tune_s = time.time() - t0
+    plans = [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, device=dev)
+             for c, wl in zip(choices, wls)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step_batched():
+        ys = forward_batched(plans, ps, ws, qs)
+        backward_batched(plans, ps, ws, qs, ys)
+
+    def step_sequential():
+        for pl, p, w, q in zip(plans, ps, ws, qs):
+            y = pl.forward(p, w, q)
+            pl.backward(p, w, q, y)
+
+    def timed(fn):
+        for _ in range(max(3, warmup)):
+            fn()
+        torch.cuda.synchronize(dev)
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            total += a.elapsed_time(b)
+        return total / steps
+
+    ms = timed(step_batched)
+    ms_seq = timed(step_sequential)
+    queries = sum(wl.M for wl in wls)
+    hist = {}
+    for c in choices:
+        key = f"{c.grid}^3 order {c.order}"
+        hist[key] = hist.get(key, 0) + 1
+    for pl in plans:
+        pl.close()
+    return {"workload": f"mixture, {n_inst} instances", "instances": n_inst, "queries": queries,
+            "sigma": wls[0].sigma, "choices": hist, "autotune_s": tune_s,
+            "value": queries / (ms / 1e3), "unit": "query-evals/s (fwd+bwd, all instances)",
+            "ms_per_step": ms, "steps": steps,
+            "one_stream": {"ms_per_step": ms_seq, "value": queries / (ms_seq / 1e3)}}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -511,6 +574,7 @@ def run_ours(args, rank, world, local_rank):
         variants["bf16x3_fit"] = measure_mode("bf16x3", wl, args, world, dev, flush, ref=ref_fit,
                                               steps=min(args.steps, 10), fit=True)
     rays = measure_rays(dev, flush, min(args.steps, 10), args.warmup) if (args.m2l == "auto" and rank == 0) else None
+    batched = measure_batched(dev, flush, min(args.steps, 5), args.warmup) if (args.m2l == "auto" and rank == 0) else None
     if rank != 0:
         return
     peaks = load_peaks()
@@ -551,6 +615,7 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms_per_step": main.stage_ms,
         "variants": {k: summary(v) for k, v in variants.items()},
         "ray_integrals": rays,
+        "batched": batched,
         "cpu_baseline": cpu,
     }
     print(json.dumps(line), flush=True)

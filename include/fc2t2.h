@@ -258,11 +258,15 @@ FC2T2_API fc2t2_status fc2t2_ray_backward(fc2t2_plan plan, void *stream, const f
 
 /* Batched forms (independent instances of uneven size, e.g. many small point sets): instance i
  * uses plans[i] and the device arrays p[i], w[i], q[i], y[i] (host arrays of device pointers,
- * each of n_inst entries) with N[i] sources and M[i] queries.  All instances are enqueued on
- * `stream` in order; the call is equivalent to n_inst calls of fc2t2_forward / fc2t2_backward and
- * can be captured into a CUDA graph by the caller (with check_domain off).  Two instances may
- * share a plan (they run one after the other).  Errors: INVALID_ARG (n_inst < 0, a NULL array),
- * and any error of the single-instance call, for the first failing instance. */
+ * each of n_inst entries) with N[i] sources and M[i] queries.  The call forks `stream` into one
+ * stream per distinct plan (each plan owns one): a plan's instances run on its stream in order,
+ * instances of different plans side by side (small instances fill the GPU together), and every
+ * plan stream is joined back into `stream` before the call returns, so work enqueued on `stream`
+ * afterwards sees all results.  The call is equivalent to n_inst calls of fc2t2_forward /
+ * fc2t2_backward and can be captured into a CUDA graph by the caller (with check_domain off: the
+ * fork / join become parallel branches).  Errors: INVALID_ARG (n_inst < 0, a NULL array or plan),
+ * and any error of the single-instance call, for the first failing instance (the remaining
+ * instances are not enqueued; the plan streams are joined all the same). */
 FC2T2_API fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream,
                                              const float *const *p, const float *const *w, const int64_t *N,
                                              const float *const *q, const int64_t *M, float *const *y);

@@ -1,5 +1,6 @@
 // C ABI of the FC2T2 library: plan creation (operator tables, workspace) and the
 // forward / backward pipelines (Sec. 3 and Sec. 4.1 of arXiv 2111.00110).
+#include <atomic>
 #include <cmath>
 #include <memory>
 #include <cstdio>
@@ -264,6 +265,9 @@ static void destroy(fc2t2_plan_s *pl) {
     if (pl->ev_fork) cudaEventDestroy(pl->ev_fork);
     if (pl->ev_join) cudaEventDestroy(pl->ev_join);
     if (pl->ev_sorted) cudaEventDestroy(pl->ev_sorted);
+    if (pl->run) cudaStreamDestroy(pl->run);
+    if (pl->ev_run_fork) cudaEventDestroy(pl->ev_run_fork);
+    if (pl->ev_run_done) cudaEventDestroy(pl->ev_run_done);
     cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
     cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
     cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
@@ -648,6 +652,12 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
     pl->src.scan_tmp = pl->d_scan_tmp;
     pl->qry.scan_tmp = pl->d_scan_tmp + tmp;
     if ((st = build_tables(pl)) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = check_cuda(cudaStreamCreateWithFlags(&pl->run, cudaStreamNonBlocking), "stream")) != FC2T2_OK ||
+        (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_run_fork, cudaEventDisableTiming), "event")) != FC2T2_OK ||
+        (st = check_cuda(cudaEventCreateWithFlags(&pl->ev_run_done, cudaEventDisableTiming), "event")) != FC2T2_OK) {
+        destroy(pl);
+        return st;
+    }
     if (pl->sep.enabled) {
         int lo_prio = 0, hi_prio = 0;
         cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
@@ -963,17 +973,54 @@ fc2t2_status fc2t2_profile_read(fc2t2_plan pl, double *ms, int64_t *launches, in
     return st;
 }
 
+namespace {
+
+// Fork the call's stream into the stream of every distinct plan of a batch (in order of first
+// appearance), so instances of different plans run side by side; join them back at the end.
+std::atomic<uint64_t> g_batch_counter{0};
+
+fc2t2_status batch_fork(int n_inst, const fc2t2_plan *plans, cudaStream_t s, uint64_t mark) {
+    for (int i = 0; i < n_inst; ++i) {
+        fc2t2_plan_s *pl = plans[i];
+        if (pl->batch_mark == mark) continue;
+        pl->batch_mark = mark;
+        fc2t2_status st;
+        if ((st = check_cuda(cudaEventRecord(pl->ev_run_fork, s), "fork")) != FC2T2_OK) return st;
+        if ((st = check_cuda(cudaStreamWaitEvent(pl->run, pl->ev_run_fork, 0), "fork")) != FC2T2_OK) return st;
+    }
+    return FC2T2_OK;
+}
+
+fc2t2_status batch_join(int n_inst, const fc2t2_plan *plans, cudaStream_t s, uint64_t mark) {
+    fc2t2_status first = FC2T2_OK;
+    for (int i = 0; i < n_inst; ++i) {   // (every forked stream rejoins, even after an error)
+        fc2t2_plan_s *pl = plans[i];
+        if (pl->batch_mark != mark) continue;
+        pl->batch_mark = 0;
+        fc2t2_status st = check_cuda(cudaEventRecord(pl->ev_run_done, pl->run), "join");
+        if (st == FC2T2_OK) st = check_cuda(cudaStreamWaitEvent(s, pl->ev_run_done, 0), "join");
+        if (first == FC2T2_OK) first = st;
+    }
+    return first;
+}
+
+}  // namespace
+
 fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
                                    float *const *y) {
     if (n_inst < 0) return set_error(FC2T2_ERR_INVALID_ARG, "n_inst < 0");
     if (n_inst == 0) return FC2T2_OK;
     if (!plans || !p || !w || !N || !q || !M || !y) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
-    for (int i = 0; i < n_inst; ++i) {
-        const fc2t2_status st = fc2t2_forward(plans[i], stream, p[i], w[i], N[i], q[i], M[i], y[i]);
-        if (st != FC2T2_OK) return st;
-    }
-    return FC2T2_OK;
+    for (int i = 0; i < n_inst; ++i)
+        if (!plans[i]) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t mark = ++g_batch_counter;
+    fc2t2_status st = batch_fork(n_inst, plans, s, mark);
+    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
+        st = fc2t2_forward(plans[i], plans[i]->run, p[i], w[i], N[i], q[i], M[i], y[i]);
+    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+    return st != FC2T2_OK ? st : sj;
 }
 
 fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
@@ -983,11 +1030,15 @@ fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *s
     if (n_inst == 0) return FC2T2_OK;
     if (!plans || !p || !w || !N || !q || !M || !ybar || !wbar || !pbar)
         return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
-    for (int i = 0; i < n_inst; ++i) {
-        const fc2t2_status st = fc2t2_backward(plans[i], stream, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
-        if (st != FC2T2_OK) return st;
-    }
-    return FC2T2_OK;
+    for (int i = 0; i < n_inst; ++i)
+        if (!plans[i]) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const uint64_t mark = ++g_batch_counter;
+    fc2t2_status st = batch_fork(n_inst, plans, s, mark);
+    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
+        st = fc2t2_backward(plans[i], plans[i]->run, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
+    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+    return st != FC2T2_OK ? st : sj;
 }
 
 fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {

@@ -154,6 +154,11 @@ struct fc2t2_plan_s {
     // passes (fork / join by events on the call's stream)
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_sorted = nullptr;
+    // batched calls: the plan's instances run on its own stream, forked from and joined to the
+    // call's stream (instances of different plans overlap)
+    cudaStream_t run = nullptr;
+    cudaEvent_t ev_run_fork = nullptr, ev_run_done = nullptr;
+    uint64_t batch_mark = 0;
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
     float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
     float *d_pow2 = nullptr;      // [P]  2^-|a|

@@ -110,6 +110,49 @@ def test_batched_empty_and_single(lib):
     assert rel_l2(yb.cpu().numpy(), y.cpu().numpy()) <= 1e-6
 
 
+def test_batched_streams_shared_plan_and_graph(lib):
+    """A batch forks one stream per distinct plan: two instances sharing a plan still run in order
+    (each result equals its own unbatched call), and a batched forward + backward captured in a
+    CUDA graph (the plan streams become parallel branches) replays to the eager results."""
+    from paper_2111_00110_gb300.transform import backward_batched, forward_batched
+    wls = [workloads.mixture(i, grid=32, order=o, n_override=n) for i, o, n in ((6, 4, 5000), (7, 6, 9000),
+                                                                                 (8, 4, 3000), (9, 6, 7000))]
+    plans = [make_plan(3, 32, wl.order, wl.sigma, 10000, 10000, m2l=m) for wl, m in zip(wls[:3], ("separable", "bf16x3", "fp32"))]
+    use = [plans[0], plans[1], plans[2], plans[1]]       # instances 1 and 3 share a plan (both order 6)
+    ps, ws, qs = [dev(wl.p) for wl in wls], [dev(wl.w) for wl in wls], [dev(wl.q) for wl in wls]
+    ys = forward_batched(use, ps, ws, qs)
+    torch.cuda.synchronize()
+    for pl, p, w, q, y in zip(use, ps, ws, qs, ys):
+        ye = pl.forward(p, w, q)
+        torch.cuda.synchronize()
+        assert rel_l2(y.cpu().numpy(), ye.cpu().numpy()) <= 1e-6
+    ybars = [dev(wl.ybar()) for wl in wls]
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):                      # warm up outside capture
+        forward_batched(use, ps, ws, qs)
+        backward_batched(use, ps, ws, qs, ybars)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        yg = forward_batched(use, ps, ws, qs)
+        gg = backward_batched(use, ps, ws, qs, ybars)
+    g.replay()
+    torch.cuda.synchronize()
+    ye = forward_batched(use, ps, ws, qs)
+    ge = backward_batched(use, ps, ws, qs, ybars)
+    torch.cuda.synchronize()
+    for a, b in zip(yg, ye):
+        assert rel_l2(a.cpu().numpy(), b.cpu().numpy()) <= 1e-6
+    for (wa, pa), (wb, pb) in zip(gg, ge):
+        assert rel_l2(wa.cpu().numpy(), wb.cpu().numpy()) <= 1e-6
+        assert rel_l2(pa.cpu().numpy(), pb.cpu().numpy()) <= 1e-6
+    del g
+    for pl in plans:
+        pl.close()
+
+
 # ------------------------------------------------------------------ CUDA graph replay
 
 @pytest.mark.parametrize("mode", ["separable", "bf16x3"])
