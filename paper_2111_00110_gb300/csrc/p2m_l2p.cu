@@ -17,6 +17,7 @@
 // Sec. 4.1), and writes results back in input order through the sort permutation.
 #include "dispatch.cuh"
 #include "fc2t2_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fc2t2 {
 
@@ -144,39 +145,48 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
                                                             const float *__restrict__ L1, int n, float lo,
                                                             float scale, float h0, float inv_h0, float h1,
                                                             float inv_h1, float *__restrict__ val,
-                                                            float *__restrict__ grad, int accumulate) {
+                                                            float *__restrict__ grad, int accumulate,
+                                                            int *__restrict__ err) {
     constexpr int Pp = pad4(ncoef(D, RHO)), P4 = Pp / 4;
-    __shared__ float4 rows[(kStageCells + (TWO ? kStageCells / 2 : 0)) * P4];
+    __shared__ alignas(16) float4 rows[(kStageCells + (TWO ? kStageCells / 2 : 0)) * P4];
+    __shared__ uint64_t staged;   // mbarrier: the bulk copies of the rows have landed
     const int sc = n < kStageCells ? n : kStageCells;
     const int64_t c0 = (int64_t)blockIdx.x * sc;          // first cell (x0 = c0 mod n, a multiple of sc)
     const int x0 = (int)(c0 % n);
-    // the segment's points, and this thread's first record, are loaded before the rows are staged
     const int j0 = __ldg(start + c0), j1 = __ldg(start + c0 + sc);
-    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
-    int in = 0;                                            // and its place in the input order
-    if (j0 + (int)threadIdx.x < j1) {
-        rn = __ldg(rec + j0 + threadIdx.x);
-        in = __ldg(perm + j0 + threadIdx.x);
-    }
-    // stage the segment's rows (and its parents' rows)
-    {
-        const float4 *src0 = reinterpret_cast<const float4 *>(L0 + c0 * Pp);
-        for (int i = threadIdx.x; i < sc * P4; i += kL2PThreads) rows[i] = __ldg(src0 + i);
+    if (j0 == j1) return;                                  // no points in the segment: nothing to stage
+    // stage the segment's rows (and its parents' rows): both are contiguous in memory, so one
+    // thread issues bulk asynchronous copies (16-byte aligned, multiples of 16 bytes) that complete
+    // on an mbarrier, while every thread fetches its first point
+    if (threadIdx.x == 0) tc::mbar_init(&staged, 1);
+    tc::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t b0 = (uint32_t)(sc * Pp * sizeof(float));
+        uint32_t b1 = 0;
+        int64_t p0 = 0;
         if (TWO) {
             const int n1 = n >> 1;
-            int64_t rest = c0 / n, p0 = 0;                 // (y, z) of the line, then the parent line
-            int64_t mul = n1;
+            int64_t rest = c0 / n, mul = n1;               // (y, z) of the line, then the parent line
             for (int d = 1; d < D; ++d) {
                 p0 += (rest % n >> 1) * mul;
                 rest /= n;
                 mul *= n1;
             }
             p0 += x0 >> 1;
-            const float4 *src1 = reinterpret_cast<const float4 *>(L1 + p0 * Pp);
-            for (int i = threadIdx.x; i < (sc >> 1) * P4; i += kL2PThreads) rows[sc * P4 + i] = __ldg(src1 + i);
+            b1 = (uint32_t)((sc >> 1) * Pp * sizeof(float));
         }
+        tc::mbar_arrive_expect_tx(&staged, b0 + b1);
+        tc::bulk_g2s(rows, L0 + c0 * Pp, b0, &staged);
+        if (TWO) tc::bulk_g2s(rows + sc * P4, L1 + p0 * Pp, b1, &staged);
     }
-    __syncthreads();
+    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+    int in = 0;                                            // and its place in the input order
+    if (j0 + (int)threadIdx.x < j1) {
+        rn = __ldg(rec + j0 + threadIdx.x);
+        in = __ldg(perm + j0 + threadIdx.x);
+    }
+    if (!tc::mbar_wait(&staged, 0, err, 512)) return;     // (bounded; a timeout is reported by the plan)
     for (int j = j0 + threadIdx.x; j < j1; j += kL2PThreads) {
         const float4 r = rn;
         const int i_out = in;
@@ -252,14 +262,14 @@ static cudaError_t launch_l2p_staged(const fc2t2_plan_s *pl, cudaStream_t s, con
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p_staged<D_, R_, true, TWO><<<blocks, kL2PThreads, 0, s>>>(
                             w.rec, w.perm, w.start, L0, L1, pl->n, pl->lo_f, pl->scale0_f, h0, inv_h0, h1, inv_h1,
-                            val, grad_times_w, accumulate ? 1 : 0),
+                            val, grad_times_w, accumulate ? 1 : 0, pl->d_flags + 2),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     } else {
         FC2T2_DISPATCH(pl->D, pl->rho,
                        (k_l2p_staged<D_, R_, false, TWO><<<blocks, kL2PThreads, 0, s>>>(
                             w.rec, w.perm, w.start, L0, L1, pl->n, pl->lo_f, pl->scale0_f, h0, inv_h0, h1, inv_h1,
-                            val, nullptr, 0),
+                            val, nullptr, 0, pl->d_flags + 2),
                         err = cudaGetLastError()),
                        return cudaErrorInvalidValue)
     }
