@@ -27,12 +27,28 @@ template <int D, int RHO>
 __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ rec,
                                                      const int *__restrict__ start, int n,
                                                      int64_t G, float lo, float h, float inv_h,
-                                                     float *__restrict__ M) {
+                                                     float *__restrict__ M, int *__restrict__ err) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
-    extern __shared__ float4 smem4[];
+    extern __shared__ float4 smem4[];   // the block's sorted records, then its output rows
+    __shared__ uint64_t staged;
     float *sm = reinterpret_cast<float *>(smem4);
     const int64_t c0 = (int64_t)blockIdx.x * kP2MThreads;
     const int64_t c = c0 + threadIdx.x;
+    // The records of the block's cells are contiguous in the sort: one bulk asynchronous copy
+    // stages them (as many as fit the output buffer) while the threads set up their cells; records
+    // past the staged ones, or all of them if the bounded wait gives up, are read from memory.
+    const int64_t c_end = (G - c0) < kP2MThreads ? G : c0 + kP2MThreads;
+    const int jb0 = __ldg(start + c0), jb1 = __ldg(start + c_end);
+    const int nst = min(jb1 - jb0, kP2MThreads * Pp / 4);
+    if (nst > 0) {
+        if (threadIdx.x == 0) tc::mbar_init(&staged, 1);
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc::mbar_arrive_expect_tx(&staged, (uint32_t)nst * 16u);
+            tc::bulk_g2s(smem4, rec + jb0, (uint32_t)nst * 16u, &staged);
+        }
+    }
     float acc[P];
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = 0.0f;
@@ -45,12 +61,9 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
 #pragma unroll
         for (int d = 0; d < D; ++d) z[d] = lo + ((float)cc[d] + 0.5f) * h;
         const int j0 = start[c], j1 = start[c + 1];
-        // each source's record is loaded one iteration ahead (its latency behind the previous
-        // source's arithmetic)
-        float4 rn = j0 < j1 ? __ldg(rec + j0) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const bool have = nst > 0 && j1 > j0 && tc::mbar_wait(&staged, 0, err, 1024);
         for (int j = j0; j < j1; ++j) {
-            const float4 r = rn;
-            if (j + 1 < j1) rn = __ldg(rec + j + 1);
+            const float4 r = (have && j - jb0 < nst) ? smem4[j - jb0] : __ldg(rec + j);
             const float xj[3] = {r.x, r.y, r.z};
             float pw[3][RHO + 1];
 #pragma unroll
@@ -76,6 +89,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
             }
         }
     }
+    __syncthreads();   // every staged record has been read before the buffer takes the output rows
 #pragma unroll
     for (int k = 0; k < Pp; ++k) sm[threadIdx.x * Pp + k] = (k < P) ? acc[k] : 0.0f;
     __syncthreads();
@@ -94,7 +108,7 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     pl->launches[FC2T2_STAGE_P2M] += 1;
     FC2T2_DISPATCH(pl->D, pl->rho,
                    (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.rec, w.start, pl->n, G,
-                                                                    pl->lo_f, h, inv_h, M0),
+                                                                    pl->lo_f, h, inv_h, M0, pl->d_flags + 2),
                     err = cudaGetLastError()),
                    return cudaErrorInvalidValue)
     return err;
