@@ -268,9 +268,7 @@ static void destroy(fc2t2_plan_s *pl) {
     if (pl->run) cudaStreamDestroy(pl->run);
     if (pl->ev_run_fork) cudaEventDestroy(pl->ev_run_fork);
     if (pl->ev_run_done) cudaEventDestroy(pl->ev_run_done);
-    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_shift);
-    cudaFree(pl->d_pow2); cudaFree(pl->d_m2m_start); cudaFree(pl->d_m2m_pairs);
-    cudaFree(pl->d_l2l_start); cudaFree(pl->d_l2l_pairs); cudaFree(pl->d_m2l_start);
+    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_m2l_start);
     cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
     cudaFree(pl->d_mma_ops);
     for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
@@ -305,35 +303,11 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
             }
         }
     }
-    // child re-centring: shift[ch][g] = prod_d s_d^(g_d) / g_d!,  s_d = +1/2 (odd child) or -1/2
-    std::vector<float> shift((size_t)(1 << D) * P);
-    for (int ch = 0; ch < (1 << D); ++ch)
-        for (int g = 0; g < P; ++g) {
-            double v = 1.0;
-            for (int d = 0; d < D; ++d) {
-                const double s = ((ch >> d) & 1) ? 0.5 : -0.5;
-                for (int t = 1; t <= ix.e[3 * g + d]; ++t) v *= s / t;
-            }
-            shift[(size_t)ch * P + g] = (float)v;
-        }
-    std::vector<float> pow2(P);
-    for (int k = 0; k < P; ++k) pow2[k] = (float)std::ldexp(1.0, -ix.deg[k]);
-
-    std::vector<int> m2m_start(P + 1), l2l_start(P + 1), m2l_start(P + 1);
-    std::vector<int2> m2m_pairs, l2l_pairs, m2l_pairs;
+    // M2L pair lists of the CUDA-core form: for every output k, the b with |k| + |b| <= rho and
+    // the index of k + b
+    std::vector<int> m2l_start(P + 1);
+    std::vector<int2> m2l_pairs;
     for (int a = 0; a < P; ++a) {
-        m2m_start[a] = (int)m2m_pairs.size();
-        for (int b = 0; b < P; ++b) {
-            const int g = ix.index(ix.e[3 * a] - ix.e[3 * b], ix.e[3 * a + 1] - ix.e[3 * b + 1],
-                                   ix.e[3 * a + 2] - ix.e[3 * b + 2]);
-            if (g >= 0) m2m_pairs.push_back(make_int2(b, g));
-        }
-        l2l_start[a] = (int)l2l_pairs.size();
-        for (int g = 0; g < P; ++g) {
-            const int dlt = ix.index(ix.e[3 * g] - ix.e[3 * a], ix.e[3 * g + 1] - ix.e[3 * a + 1],
-                                     ix.e[3 * g + 2] - ix.e[3 * a + 2]);
-            if (dlt >= 0) l2l_pairs.push_back(make_int2(g, dlt));
-        }
         m2l_start[a] = (int)m2l_pairs.size();
         for (int b = 0; b < P; ++b) {
             if (ix.deg[a] + ix.deg[b] > rho) continue;
@@ -342,29 +316,13 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
             m2l_pairs.push_back(make_int2(b, kb));
         }
     }
-    m2m_start[P] = (int)m2m_pairs.size();
-    l2l_start[P] = (int)l2l_pairs.size();
-    pl->n_m2m_pairs = (int)m2m_pairs.size();
-    pl->n_l2l_pairs = (int)l2l_pairs.size();
     m2l_start[P] = (int)m2l_pairs.size();
 
     fc2t2_status st;
     if ((st = dev_alloc(&pl->d_dtab, dtab.size(), "derivative tables")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_shift, shift.size(), "shift tables")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_pow2, pow2.size(), "scales")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_m2m_start, m2m_start.size(), "m2m index")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_m2m_pairs, m2m_pairs.size(), "m2m pairs")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_l2l_start, l2l_start.size(), "l2l index")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_l2l_pairs, l2l_pairs.size(), "l2l pairs")) != FC2T2_OK) return st;
     if ((st = dev_alloc(&pl->d_m2l_start, m2l_start.size(), "m2l index")) != FC2T2_OK) return st;
     if ((st = dev_alloc(&pl->d_m2l_pairs, m2l_pairs.size(), "m2l pairs")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_dtab, dtab, "upload derivative tables")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_shift, shift, "upload shift tables")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_pow2, pow2, "upload scales")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_m2m_start, m2m_start, "upload m2m index")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_m2m_pairs, m2m_pairs, "upload m2m pairs")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_l2l_start, l2l_start, "upload l2l index")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_l2l_pairs, l2l_pairs, "upload l2l pairs")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_m2l_start, m2l_start, "upload m2l index")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_m2l_pairs, m2l_pairs, "upload m2l pairs")) != FC2T2_OK) return st;
     // tensor-core operator images (3D; other dimensions keep the CUDA-core M2L)

@@ -160,14 +160,6 @@ struct fc2t2_plan_s {
     cudaEvent_t ev_run_fork = nullptr, ev_run_done = nullptr;
     uint64_t batch_mark = 0;
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
-    float *d_shift = nullptr;     // [2^D][P]  s^g / g!  for the M2M / L2L re-centring
-    float *d_pow2 = nullptr;      // [P]  2^-|a|
-    int *d_m2m_start = nullptr;   // [P+1]  per a: pairs (b, a-b) with b <= a
-    int2 *d_m2m_pairs = nullptr;
-    int n_m2m_pairs = 0;
-    int *d_l2l_start = nullptr;   // [P+1]  per k: pairs (g, g-k) with g >= k
-    int2 *d_l2l_pairs = nullptr;
-    int n_l2l_pairs = 0;
     int *d_m2l_start = nullptr;   // [P+1]  per k: pairs (b, k+b) with |b| <= rho-|k|
     int2 *d_m2l_pairs = nullptr;
     int *d_scan_tmp = nullptr;    // block sums of the prefix scan

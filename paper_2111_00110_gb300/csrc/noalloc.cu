@@ -44,8 +44,7 @@ constexpr size_t kSortBytes =
 constexpr size_t kScratchBytes =
     2 * align256(sizeof(float) * kNaMaxCellsAllLevels * kNaMaxPp) +                  // M, L
     align256(sizeof(float) * kNaMaxLevels * kNaOffsets * kNaMaxPp) +                 // dtab
-    align256(sizeof(float) * 8 * kNaMaxPp) + align256(sizeof(float) * kNaMaxPp) +    // shift, 2^-|a|
-    3 * (align256(sizeof(int) * (kNaMaxPp + 1)) + align256(sizeof(int2) * kNaMaxPairs)) +
+    align256(sizeof(int) * (kNaMaxPp + 1)) + align256(sizeof(int2) * kNaMaxPairs) +  // M2L pairs
     align256(sizeof(int) * 64) + align256(sizeof(int) * 4) +                         // scan, flags
     2 * kSortBytes;
 
@@ -61,10 +60,8 @@ void *g_na_addr[128] = {nullptr};      // device address of the scratch array, p
 
 // host staging of the operator tables (static storage, no allocation)
 float h_dtab[kNaMaxLevels * kNaOffsets * kNaMaxPp];
-float h_shift[8 * kNaMaxPp];
-float h_pow2[kNaMaxPp];
-int h_start[3][kNaMaxPp + 1];
-int2 h_pairs[3][kNaMaxPairs];
+int h_start[kNaMaxPp + 1];
+int2 h_pairs[kNaMaxPairs];
 
 struct SmallIndex {
     int D, rho, P;
@@ -183,17 +180,8 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     pl.d_M = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
     pl.d_L = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
     pl.d_dtab = carve<float>(base, off, (size_t)kNaMaxLevels * kNaOffsets * kNaMaxPp);
-    pl.d_shift = carve<float>(base, off, 8 * kNaMaxPp);
-    pl.d_pow2 = carve<float>(base, off, kNaMaxPp);
-    int *starts[3];
-    int2 *pairs[3];
-    for (int t = 0; t < 3; ++t) {
-        starts[t] = carve<int>(base, off, kNaMaxPp + 1);
-        pairs[t] = carve<int2>(base, off, kNaMaxPairs);
-    }
-    pl.d_m2m_start = starts[0]; pl.d_m2m_pairs = pairs[0];
-    pl.d_l2l_start = starts[1]; pl.d_l2l_pairs = pairs[1];
-    pl.d_m2l_start = starts[2]; pl.d_m2l_pairs = pairs[2];
+    pl.d_m2l_start = carve<int>(base, off, kNaMaxPp + 1);
+    pl.d_m2l_pairs = carve<int2>(base, off, kNaMaxPairs);
     pl.d_scan_tmp = carve<int>(base, off, 64);
     pl.d_flags = carve<int>(base, off, 4);
     SortWork *sorts[2] = {&pl.src, &pl.qry};
@@ -226,47 +214,21 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
             }
         }
     }
-    for (int ch = 0; ch < (1 << D); ++ch)
-        for (int gg = 0; gg < P; ++gg) {
-            double v = 1.0;
-            for (int d = 0; d < D; ++d) {
-                const double sg = ((ch >> d) & 1) ? 0.5 : -0.5;
-                for (int t = 1; t <= ix.e[gg][d]; ++t) v *= sg / t;
-            }
-            h_shift[ch * P + gg] = (float)v;
-        }
-    for (int k = 0; k < P; ++k) h_pow2[k] = (float)std::ldexp(1.0, -ix.deg[k]);
-    int cnt[3] = {0, 0, 0};
+    int cnt = 0;   // the M2L pair lists, as a plan's
     for (int a = 0; a < P; ++a) {
-        h_start[0][a] = cnt[0];
-        for (int b = 0; b < P; ++b) {
-            const int gg = ix.index(ix.e[a][0] - ix.e[b][0], ix.e[a][1] - ix.e[b][1], ix.e[a][2] - ix.e[b][2]);
-            if (gg >= 0) h_pairs[0][cnt[0]++] = make_int2(b, gg);
-        }
-        h_start[1][a] = cnt[1];
-        for (int gg = 0; gg < P; ++gg) {
-            const int dl = ix.index(ix.e[gg][0] - ix.e[a][0], ix.e[gg][1] - ix.e[a][1], ix.e[gg][2] - ix.e[a][2]);
-            if (dl >= 0) h_pairs[1][cnt[1]++] = make_int2(gg, dl);
-        }
-        h_start[2][a] = cnt[2];
+        h_start[a] = cnt;
         for (int b = 0; b < P; ++b) {
             if (ix.deg[a] + ix.deg[b] > pl.rho) continue;
-            h_pairs[2][cnt[2]++] = make_int2(b, ix.index(ix.e[a][0] + ix.e[b][0], ix.e[a][1] + ix.e[b][1],
-                                                         ix.e[a][2] + ix.e[b][2]));
+            h_pairs[cnt++] = make_int2(b, ix.index(ix.e[a][0] + ix.e[b][0], ix.e[a][1] + ix.e[b][1],
+                                                   ix.e[a][2] + ix.e[b][2]));
         }
     }
-    for (int t = 0; t < 3; ++t) h_start[t][P] = cnt[t];
-    pl.n_m2m_pairs = cnt[0];
-    pl.n_l2l_pairs = cnt[1];
+    h_start[P] = cnt;
 
     // pageable host-to-device copies return once the host data has been staged
     struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
         {pl.d_dtab, h_dtab, sizeof(float) * (size_t)pl.nlev * nofs * Pp},
-        {pl.d_shift, h_shift, sizeof(float) * (size_t)(1 << D) * P},
-        {pl.d_pow2, h_pow2, sizeof(float) * (size_t)P},
-        {starts[0], h_start[0], sizeof(int) * (size_t)(P + 1)}, {pairs[0], h_pairs[0], sizeof(int2) * (size_t)cnt[0]},
-        {starts[1], h_start[1], sizeof(int) * (size_t)(P + 1)}, {pairs[1], h_pairs[1], sizeof(int2) * (size_t)cnt[1]},
-        {starts[2], h_start[2], sizeof(int) * (size_t)(P + 1)}, {pairs[2], h_pairs[2], sizeof(int2) * (size_t)cnt[2]},
+        {pl.d_m2l_start, h_start, sizeof(int) * (size_t)(P + 1)}, {pl.d_m2l_pairs, h_pairs, sizeof(int2) * (size_t)cnt},
     };
     for (const Up &u : ups)
         if ((st = check_cuda(cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, s), "upload tables")) != FC2T2_OK)
