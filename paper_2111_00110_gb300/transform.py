@@ -35,15 +35,25 @@ def _check_tensor(t: torch.Tensor, name: str, shape) -> None:
         raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
 
 
+def resolve_m2l(m2l: str, dim: int, kernel: str, fit: bool) -> str:
+    """The M2L form of a plan: "auto" takes the separable line passes where they apply (the
+    Gaussian in 3D with Taylor operators: the fastest form, at FP32 accuracy), else plain FP32."""
+    if m2l != "auto":
+        return m2l
+    return "separable" if (kernel == "gaussian" and dim == 3 and not fit) else "fp32"
+
+
 class Plan:
-    """A transform plan: dimension, finest grid, order, kernel, domain, workspace bounds."""
+    """A transform plan: dimension, finest grid, order, kernel, domain, workspace bounds, M2L form
+    ("auto", "separable", "fp32", "tf32", "bf16", "tf32x3", "bf16x3")."""
 
     def __init__(self, dim: int, grid: int, order: int, sigma: float = 0.05, *,
                  kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
-                 lo: float = 0.0, hi: float = 1.0, m2l: str = "fp32", check_domain: bool = False,
+                 lo: float = 0.0, hi: float = 1.0, m2l: str = "auto", check_domain: bool = False,
                  max_sources: int = 1 << 20, max_queries: int = 1 << 20, channels: int = 1, fit: bool = False,
                  device=None):
         self.dim, self.grid, self.order, self.channels = dim, grid, order, int(channels)
+        m2l = resolve_m2l(m2l, dim, kernel, fit)
         self._serial = 0   # counts the calls that replace the plan's expansion
         self.sigma, self.kernel, self.lo, self.hi, self.m2l = sigma, kernel, lo, hi, m2l
         self.max_sources, self.max_queries = int(max_sources), int(max_queries)

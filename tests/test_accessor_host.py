@@ -1,6 +1,6 @@
 """Host-side logic of the accessor (Sec. 3, "How to use the implementation?"): how an index is
 split into the channel entry and the spatial entries, slices read as linspace, and the output
-shapes of point and volume queries.  No GPU."""
+shapes of point and volume queries; the plan's default M2L form.  No GPU."""
 import numpy as np
 import pytest
 import torch
@@ -47,3 +47,15 @@ def test_channel_selection():
     assert select_channels(out, 1).shape == (6,)
     assert select_channels(out, slice(1, 3)).shape == (2, 6)
     assert torch.equal(select_channels(out, [3, 0]), out[[3, 0]])
+
+
+def test_plan_m2l_auto_resolution():
+    """A plan's default M2L form: the separable line passes where they apply (the Gaussian in 3D
+    with Taylor operators), plain FP32 otherwise; an explicit form is kept."""
+    from paper_2111_00110_gb300.transform import resolve_m2l
+    assert resolve_m2l("auto", 3, "gaussian", False) == "separable"
+    assert resolve_m2l("auto", 2, "gaussian", False) == "fp32"
+    assert resolve_m2l("auto", 3, "poly", False) == "fp32"
+    assert resolve_m2l("auto", 3, "gaussian", True) == "fp32"
+    for form in ("fp32", "tf32", "bf16", "tf32x3", "bf16x3", "separable"):
+        assert resolve_m2l(form, 3, "gaussian", False) == form

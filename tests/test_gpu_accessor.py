@@ -45,6 +45,7 @@ def lib():
 
 def make_plan(dim, grid, order, sigma, N, M, **kw):
     from paper_2111_00110_gb300.transform import Plan
+    kw.setdefault("m2l", "fp32")
     return Plan(dim, grid, order, sigma, max_sources=max(N, 1), max_queries=max(M, 1), **kw)
 
 

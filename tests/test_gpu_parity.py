@@ -44,6 +44,7 @@ def lib():
 
 def make_plan(dim, grid, order, sigma, N, M, **kw):
     from paper_2111_00110_gb300.transform import Plan
+    kw.setdefault("m2l", "fp32")
     return Plan(dim, grid, order, sigma, max_sources=max(N, 1), max_queries=max(M, 1), **kw)
 
 
@@ -304,6 +305,19 @@ def test_separable_m2l_backward(lib):
     wo, po = oracle.backward(odesc(3, 16, 6, wl.sigma), *f64(wl.p, wl.w, wl.q, ybar))
     assert_close(wbar, wo, what="separable wbar")
     assert_close(pbar, po, what="separable pbar")
+
+
+def test_default_plan_form(lib):
+    """A plan made without an M2L form: the separable passes for the 3D Gaussian, plain FP32 for
+    the 2D Gaussian; both against the oracle."""
+    from paper_2111_00110_gb300.transform import Plan
+    for dim, grid, order in ((3, 16, 6), (2, 32, 4)):
+        wl = workloads.uniform(779 + dim, dim, 3000, 2500, grid, order, 1.3 / grid)
+        plan = Plan(dim, grid, order, wl.sigma, max_sources=wl.N, max_queries=wl.M)
+        assert plan.m2l == ("separable" if dim == 3 else "fp32")
+        y = run_forward(plan, wl.p, wl.w, wl.q)
+        yo = oracle.forward(odesc(dim, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+        assert_close(y, yo, what=f"default plan, {dim}D")
 
 
 @pytest.mark.parametrize("mode", ["tf32x3", "bf16x3", "tf32"])

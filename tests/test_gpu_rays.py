@@ -118,7 +118,7 @@ def test_ray_empty_and_unsupported(lib):
     from paper_2111_00110_gb300 import capi
     from paper_2111_00110_gb300.transform import Plan
     p, w, rays = scene(240, 500, 4, 10)
-    plan = Plan(3, 8, 4, 0.1, max_sources=p.shape[0], max_queries=1)
+    plan = Plan(3, 8, 4, 0.1, m2l="fp32", max_sources=p.shape[0], max_queries=1)
     P_, W_, RAYS = to_dev(p, w, rays)
     assert plan.ray_forward(P_, W_, RAYS[:0].contiguous()).shape == (0,)
     y0 = plan.ray_forward(P_[:0].contiguous(), W_[:0].contiguous(), RAYS)

@@ -53,7 +53,7 @@ def noalloc_forward(lib, wl, stream):
 
 def planned_forward(wl):
     from paper_2111_00110_gb300.transform import Plan
-    plan = Plan(wl.dim, wl.grid, wl.order, wl.sigma, max_sources=wl.N, max_queries=wl.M)
+    plan = Plan(wl.dim, wl.grid, wl.order, wl.sigma, m2l="fp32", max_sources=wl.N, max_queries=wl.M)
     p, w, q = (torch.from_numpy(a).cuda() for a in (wl.p, wl.w, wl.q))
     y = plan.forward(p, w, q)
     torch.cuda.synchronize()
