@@ -398,8 +398,10 @@ struct SepPitch {
     static constexpr int sin = odd_pitch(in), sout = odd_pitch(out);                 // shared-memory row
 };
 
+// Three CTAs per multiprocessor where the registers allow it without spilling (orders <= 6, and
+// the finest pass Z at orders 7-8); two elsewhere.
 template <int RHO, int AXIS, bool FINEST>
-__global__ void __launch_bounds__(kSepThreads, RHO <= 6 ? 3 : 2) k_m2l_sep(const SepArgs args) {
+__global__ void __launch_bounds__(kSepThreads, (RHO <= 6 || (AXIS == 2 && FINEST)) ? 3 : 2) k_m2l_sep(const SepArgs args) {
     constexpr int P = ncoef(3, RHO);
     using Pt = SepPitch<RHO, AXIS>;
     constexpr bool TWO_IN = !FINEST && AXIS > 0;
@@ -648,10 +650,11 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
     // A task owns two targets at the finest level and one above it, so with segments of nt cells
     // a warp's lanes cover G = 64 / nt or 32 / nt consecutive task slots, and warp w takes the
     // slot groups w, w + W, w + 2W, ... (W warps).  Pass Y at the finest level, whose task costs
-    // spread widest (C(R+3, 3) multiply-adds per row and target: 84 at R = 6, 1 at R = 0): the
-    // pairs are grouped G at a time by equal budget (lanes of different budgets would run one
-    // after the other), and the groups are dealt longest first to the warp with the least work
-    // so far -- the CTA's compute phase ends with its busiest warp.  Unfilled slots hold (-1, -1).
+    // spread widest (C(R+3, 3) multiply-adds per row and target: 84 at R = 6, 1 at R = 0), and at
+    // orders 7-8 every pass of the finest level (165 at R = 8): the pairs are grouped G at a time
+    // by equal budget (lanes of different budgets would run one after the other), and the groups
+    // are dealt longest first to the warp with the least work so far -- the CTA's compute phase
+    // ends with its busiest warp.  Unfilled slots hold (-1, -1).
     constexpr int W = kSepThreads / 32;
     const int seg = std::min(pl->sep.seg[l_begin], pl->lev[l_begin].n);
     const int G = std::max(1, (l_begin == 0 ? 64 : 32) / seg);
@@ -665,9 +668,9 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
             groups.push_back({c, std::vector<int2>(same.begin() + k, same.begin() + std::min(same.size(), k + G))});
     }
     std::stable_sort(groups.begin(), groups.end(), [](const Group &x, const Group &y) { return x.cost > y.cost; });
-    if (!(axis == 1 && l_begin == 0)) {
-        // elsewhere (passes X and Z, and the levels above the finest, where a padded table's
-        // extra rounds cost more than the balance gains): the pairs in cost order, dealt to the
+    if (!(l_begin == 0 && (axis == 1 || pl->rho >= 7))) {
+        // elsewhere (passes X and Z at orders <= 6, and the levels above the finest, where a
+        // padded table's extra rounds cost more than the balance gains): the pairs in cost order, dealt to the
         // warps in a snake order (0, 1, .., W-1, W-1, .., 0, ...) G slots at a time
         const int T2 = tri_count(rho);
         std::vector<int> used(T2, 0);
