@@ -86,11 +86,13 @@ __device__ __forceinline__ void store_row(float *__restrict__ dst, const float (
                             4 * i + 2 < P ? a[4 * i + 2] : 0.0f, 4 * i + 3 < P ? a[4 * i + 3] : 0.0f);
 }
 
-template <int D, int RHO>
-__device__ __forceinline__ float pow2_neg_deg(int k) {
+// total degree of the coefficient at graded index k (compile-time inside unrolled loops: a loop
+// over the degrees with an inner loop over each degree's indices is not fully unrolled at orders
+// 7-8, which leaves the row indexed at run time, i.e. in local memory)
+__host__ __device__ constexpr int coef_degree(int D, int k) {
     int d = 0;
     while (ncoef(D, d) <= k) ++d;
-    return 1.0f / (float)(1 << d);
+    return d;
 }
 
 // M2M at large levels: one thread per parent cell, its children loaded and shifted in turn.
@@ -121,11 +123,7 @@ __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, f
     }
     // 2^-|a| of the parent's larger cell width
 #pragma unroll
-    for (int dg = 0; dg <= RHO; ++dg) {
-        const float sc = 1.0f / (float)(1 << dg);
-#pragma unroll
-        for (int k = (dg == 0 ? 0 : ncoef(D, dg - 1)); k < ncoef(D, dg); ++k) acc[k] *= sc;
-    }
+    for (int k = 0; k < P; ++k) acc[k] *= 1.0f / (float)(1 << coef_degree(D, k));
     store_row<D, RHO>(Mp + C * Pp, acc);
 }
 
@@ -164,12 +162,8 @@ __global__ void __launch_bounds__(256) k_m2m_child(const float *__restrict__ Mc,
     if (!valid) return;
     float *dst = Mp + C * Pp;
 #pragma unroll
-    for (int dg = 0; dg <= RHO; ++dg) {
-        const float sc = 1.0f / (float)(1 << dg);
-#pragma unroll
-        for (int k = (dg == 0 ? 0 : ncoef(D, dg - 1)); k < ncoef(D, dg); ++k)
-            if ((k & (NCH - 1)) == ch) dst[k] = a[k] * sc;
-    }
+    for (int k = 0; k < P; ++k)
+        if ((k & (NCH - 1)) == ch) dst[k] = a[k] * (1.0f / (float)(1 << coef_degree(D, k)));
 #pragma unroll
     for (int k = P; k < Pp; ++k)
         if ((k & (NCH - 1)) == ch) dst[k] = 0.0f;
@@ -192,11 +186,7 @@ __global__ void __launch_bounds__(128) k_l2l_reg(const float *__restrict__ Lp, f
     float a[P];
     load_row<D, RHO>(Lp + plin * Pp, a);
 #pragma unroll
-    for (int dg = 0; dg <= RHO; ++dg) {
-        const float sc = 1.0f / (float)(1 << dg);
-#pragma unroll
-        for (int k = (dg == 0 ? 0 : ncoef(D, dg - 1)); k < ncoef(D, dg); ++k) a[k] *= sc;
-    }
+    for (int k = 0; k < P; ++k) a[k] *= 1.0f / (float)(1 << coef_degree(D, k));
 #pragma unroll
     for (int d = 0; d < D; ++d) shift_axis<D, RHO, false>(a, d, (cc[d] & 1) ? 0.5f : -0.5f);
     float4 *own = reinterpret_cast<float4 *>(Lc + c * Pp);
