@@ -116,9 +116,10 @@ typedef struct {
                                     dimension. */
 } fc2t2_plan_desc;
 
-/* Build a plan: validate `desc`, build the M2L / M2M / L2L operator tables in FP64 on
- * the host (Sec. 3: the kernel derivatives are a once-per-plan preprocessing step, cf.
- * Sec. 3.1), cast them to the M2L precision, and allocate the device workspace for
+/* Build a plan: validate `desc`, build the M2L operator tables (the kernel's derivatives per
+ * level and offset, or their least-squares fits) in FP64 on the host (Sec. 3: the kernel
+ * derivatives are a once-per-plan preprocessing step, cf. Sec. 3.1; the M2M / L2L shifts need no
+ * table), cast them to the M2L precision, and allocate the device workspace for
  * max_sources / max_queries points.  Synchronises the current device.
  * On success *out receives the plan; on failure *out is set to NULL.
  * A plan with C > 1 channels also holds C finest-level local series for fc2t2_expand.
