@@ -40,9 +40,10 @@ METRIC = "fwd+bwd query-evals/s"
 UNIT = "query-evals/s"
 # nominal dense tensor-core ratios (TF32 : BF16 = 1.1 : 2.25 PFLOP/s per GPU)
 TF32_PER_BF16 = 1.1 / 2.25
-# DRAM bytes (read + write) of one transform's M2L launches, from an ncu capture of the current
-# kernel builds (profiles/k_m2l_sep_uniform3d.md, profiles/k_m2l_tc_bf16x3_uniform3d.md); None
-# where no capture of the current build exists
+# DRAM bytes (read + write) of one transform's M2L launches of the current kernel builds, from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the transform's M2L launches, on
+# the same grid and order at 2^18 points: the M2L launches do not depend on the point count);
+# None where no capture of the current build exists
 M2L_TRAFFIC_BYTES = {"separable": (88.1 + 12.6 + 222.3 + 63.5 + 222.4 + 63.5 + 161.8 + 5.0 + 176.4 + 16.7 + 62.2 + 1.2) * 1e6,
                      "bf16x3": (464.0 + 82.8) * 1e6}
 
@@ -400,6 +401,12 @@ def measure_e2e(plan, wl, p, w, q, nsteps, world, dev, stream):
             "serial": {"value": wl.M * nsteps * world / (serial_ms / 1e3), "ms_per_step": serial_ms / nsteps}}
 
 
+def m2l_algorithmic_bytes(P: int, levels: int, grid: int) -> int:
+    """Bytes the M2L must move per transform, whatever its form: every level's moment rows read
+    once and its local rows written once (P FP32 values per row)."""
+    return sum(2 * (grid >> l) ** 3 * P * 4 for l in range(levels))
+
+
 def separable_bytes(P: int, levels: int, grid: int) -> int:
     """Bytes the separable M2L must move per transform: every pass reads its input rows once and
     writes its output rows once (P values per Taylor row, C(order+4, 4) per 4-indexed row; one
@@ -434,12 +441,22 @@ def roofline_for(m: Measured, peaks):
         basis = "of measured hbm copy (MEASURED_PEAKS.json)"
         if hbm is None:
             hbm, basis = 6800.0, "of fallback hbm"
-        b = 2 * separable_bytes(m.info["coefficients"], m.info["levels"], m.grid)   # per step
-        gbs = b / (m2l_ms / 1e3) / 1e9
+        # algorithmic bytes of the M2L (every level's moments read once, its locals written once)
+        algo = 2 * m2l_algorithmic_bytes(m.info["coefficients"], m.info["levels"], m.grid)   # per step
+        gbs = algo / (m2l_ms / 1e3) / 1e9
+        inter = 2 * separable_bytes(m.info["coefficients"], m.info["levels"], m.grid)        # per step
+        gbs_inter = inter / (m2l_ms / 1e3) / 1e9
+        traffic = M2L_TRAFFIC_BYTES.get("separable")
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
-                "traffic": M2L_TRAFFIC_BYTES.get("separable"), "traffic_unit": "bytes per transform (6 launches)",
-                "kernel": "k_m2l_sep (passes X, Y, Z; finest level and levels above it: 6 launches per transform)",
-                "bytes_per_step": b, "useful_flops_per_step": useful,
+                "traffic": traffic, "traffic_unit": "bytes per transform (its M2L launches)",
+                "traffic_ratio": None if traffic is None else traffic / (algo / 2),
+                "kernel": "k_m2l_sep (passes X, Y, Z; finest level and levels above it)",
+                "bytes_per_step": algo,
+                "frac_with_intermediates": gbs_inter / hbm,
+                "with_intermediates": {"bytes_per_step": inter, "achieved": gbs_inter,
+                                       "what": "every pass reads its input rows and writes its output rows "
+                                               "once, the 4-indexed intermediates included"},
+                "useful_flops_per_step": useful,
                 "useful_flops_achieved_tflops": achieved, "peak_basis": basis}
     if m.mode == "fp32":
         sm = peaks.get("sm_max_mhz", 2070.0)
@@ -501,7 +518,7 @@ def stage_roofline(m: Measured, wl, peaks):
 
 
 def measure_rays(dev, flush, steps, warmup):
-    """Ray integrals (Sec. 4, integral-implicit layer) on the ray workload's sizes: 2^18 sphere-surface
+    """Ray integrals (Sec. 6, integral-implicit layer) on the ray workload's sizes: 2^18 sphere-surface
     sources, the 512 x 512 pixel rays of its pinhole camera through the cube, 64^3, order 8, sigma
     0.01, separable M2L; a step is the forward ray integrals and their adjoint (wbar, pbar for
     L = sum y^2 / 2), timed with CUDA events on the launching stream."""

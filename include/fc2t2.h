@@ -232,7 +232,8 @@ FC2T2_API fc2t2_status fc2t2_evaluate(fc2t2_plan plan, void *stream, const float
 FC2T2_API fc2t2_status fc2t2_evaluate_grid(fc2t2_plan plan, void *stream, const float *const *axis,
                                            const int64_t *count, fc2t2_eval what, float *out);
 
-/* ---- Ray integrals (Sec. 4, the integral-implicit layer: a transform integrated along rays, the
+/* ---- Ray integrals (Sec. 6, the integral-implicit layer, "Line Integral": a transform integrated
+ * along rays, each box's series first restricted to the ray (line2poly, Sec. 5, "Line to polynomial"); the
  * building block of the paper's rendering and ray-sampled losses).  Rays are R records of 8
  * floats [R][8]: origin o (3), direction r (3), t0, t1; ray q covers x(t) = o + t r for t in
  * [t0, t1] (the parameter, not arc length, is integrated), clipped to the domain box [lo, hi)^3.
@@ -246,7 +247,8 @@ FC2T2_API fc2t2_status fc2t2_evaluate_grid(fc2t2_plan plan, void *stream, const 
 FC2T2_API fc2t2_status fc2t2_ray_forward(fc2t2_plan plan, void *stream, const float *p, const float *w,
                                          int64_t N, const float *rays, int64_t R, float *y);
 
-/* The adjoint of fc2t2_ray_forward for a cotangent ybar [C][R]: the rays become the sources, each
+/* The adjoint of fc2t2_ray_forward for a cotangent ybar [C][R] (Sec. 6, "Line Integral JVP"): the
+ * rays become the sources, each
  * segment adding ybar_q times its integral of the scaled monomials to its cell's moments (the
  * paper's ray2M), and the transform is evaluated and differentiated at the sources p:
  *   wbar[c][n] = sum_q ybar[c][q] int T(p_n, x_q(t)) dt,
@@ -326,13 +328,17 @@ FC2T2_API fc2t2_status fc2t2_profile_read(fc2t2_plan plan, double *ms, int64_t *
  * holds until the process exits.  Limits: Gaussian kernel, one channel, FP32 M2L,
  * grid^dim <= 4096 finest cells (64^2 or 16^3), 1 <= order <= 4, 0 <= N, M <= 65536; larger
  * requests return FC2T2_ERR_INVALID_ARG (or FC2T2_ERR_UNSUPPORTED for other kernels) before any
- * work is queued.  desc->max_sources / max_queries / check_domain are ignored.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call outside any stream capture.  All calls share the array and it keeps the last
+ * work is queued.  desc->max_sources / max_queries are ignored; desc->check_domain must be 0
+ * (UNSUPPORTED otherwise: this path clamps points outside the domain into the edge cells and
+ * never reports them, where a plan built with check_domain returns FC2T2_ERR_DOMAIN).
+ * Every call looks up the array's device address on the current device (cudaGetSymbolAddress);
+ * the first call on a device also loads the library's device code there, so make that first
+ * call outside any stream capture.  The call queues its work on `stream` and returns without
+ * waiting for it: the operator tables are built on the device inside the array, and no host
+ * memory is read after the call returns.  All calls share the array and it keeps the last
  * call's contents (each call clears what must start from zero): calls whose work overlaps on
  * the GPU -- on different streams or from different threads -- race and give wrong results, so
- * issue them on one stream.  The call blocks until `stream` has finished earlier work (it copies
- * the operator tables from host memory).  Pointers as for fc2t2_forward.
+ * issue them on one stream, one after the other.  Pointers as for fc2t2_forward.
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
 FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *desc, void *stream,
                                              const float *p, const float *w, int64_t N,

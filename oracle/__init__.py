@@ -16,8 +16,10 @@ Public functions (all arrays are numpy, float64 unless stated):
 * ``partials(desc, p, w, q, sel=None, ...)`` -> (value, first partials, second partials) of the
     forward series at the queries (the accessor of Sec. 3, "How to use the implementation?").
 * ``ray_forward(desc, p, w, rays)`` / ``ray_backward(desc, p, w, rays, ybar)`` -> integrals of the
-    series along rays (Sec. 4, integral-implicit layer) and their adjoint (w̄, p̄).
+    series along rays (Sec. 6, integral-implicit layer) and their adjoint (w̄, p̄).
 * ``direct(desc, p, w, q, sel=None)`` -> exact O(NM) sum of Eq. 1.
+* ``direct_grad(desc, p, w, q, ybar, sel=None)`` -> (wbar, pbar) of <ybar, y> for that exact sum
+    (the dense form of Sec. 4.1's Jacobian vector product).
 * ``kernel_derivs(desc, c)`` -> d^m psi(c), |m| <= order, graded order.
 * ``fit_coeffs(desc, c, h)`` -> the least-squares fitted replacements of d^m psi(c) (``fit=True``).
 * ``multi_indices(dim, order)`` -> exponents [P, dim], graded order.
@@ -120,6 +122,9 @@ def _load():
             lib.orc_direct.argtypes = [ctypes.POINTER(_Desc), P, P, ctypes.c_int64,
                                        P, ctypes.c_int64, P, ctypes.c_int64, P]
             lib.orc_direct.restype = ctypes.c_int
+            lib.orc_direct_grad.argtypes = [ctypes.POINTER(_Desc), P, P, ctypes.c_int64,
+                                            P, P, ctypes.c_int64, P, ctypes.c_int64, P, P]
+            lib.orc_direct_grad.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -281,7 +286,7 @@ def _rays(rays):
 
 
 def ray_forward(desc: OracleDesc, p, w, rays):
-    """Sec. 4, integral-implicit layer: y_q = int_{t0}^{t1} f(o_q + t r_q) dt of the series of (p, w),
+    """Sec. 6, integral-implicit layer ("Line Integral"): y_q = int_{t0}^{t1} f(o_q + t r_q) dt of the series of (p, w),
     for rays [R, 8] (origin, direction, t0, t1; the part outside the domain box is dropped), through
     the cells each ray crosses (line2poly).  3D."""
     D = desc.dim
@@ -336,3 +341,27 @@ def direct(desc: OracleDesc, p, w, q, sel=None):
                        q.ctypes.data, q.shape[0], _ptr(sel), n_sel if sel is not None else -1,
                        val.ctypes.data)
     return val
+
+
+def direct_grad(desc: OracleDesc, p, w, q, ybar, sel=None):
+    """Gradients of <ybar, y> for the exact sum y_m = sum_n psi(p_n - q_m) w_n (Eq. 1), at the
+    selected sources: wbar_n = sum_m ybar_m psi(p_n - q_m) and
+    pbar_n = w_n sum_m ybar_m grad psi(p_n - q_m) (Sec. 4.1 applied to the dense sum)."""
+    D = desc.dim
+    p = _f64(p).reshape(-1, D)
+    q = _f64(q).reshape(-1, D)
+    w = _f64(w).reshape(-1)
+    yb = _f64(ybar).reshape(-1)
+    assert yb.shape[0] == q.shape[0] and w.shape[0] == p.shape[0]
+    if sel is not None:
+        sel = np.ascontiguousarray(sel, dtype=np.int64)
+        n_sel = sel.shape[0]
+    else:
+        n_sel = p.shape[0]
+    wbar = np.zeros(n_sel, dtype=np.float64)
+    pbar = np.zeros((n_sel, D), dtype=np.float64)
+    cd = desc.c()
+    _load().orc_direct_grad(ctypes.byref(cd), p.ctypes.data, w.ctypes.data, p.shape[0], q.ctypes.data,
+                            yb.ctypes.data, q.shape[0], _ptr(sel), n_sel if sel is not None else -1,
+                            wbar.ctypes.data, pbar.ctypes.data)
+    return wbar, pbar

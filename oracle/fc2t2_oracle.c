@@ -284,6 +284,33 @@ static double kernel_value(const orc_desc *d, const double *x) {
 }
 
 
+/* Gradient of psi at x: for the Gaussian d/dx_i psi = -(x_i / sigma^2) psi(x); for the polynomial
+ * sum_a c_a x^a the term-by-term derivative sum_a c_a a_i x^(a - e_i). */
+static void kernel_grad(const orc_desc *d, const double *x, double *g) {
+    int D = d->dim;
+    if (d->kernel == 0) {
+        double v = kernel_value(d, x), s2 = d->sigma * d->sigma;
+        for (int i = 0; i < D; ++i) g[i] = -x[i] / s2 * v;
+        return;
+    }
+    int pdeg = 0;
+    while (orc_num_coeffs(D, pdeg) < d->n_poly) ++pdeg;
+    int *pex = (int *)malloc(sizeof(int) * D * orc_num_coeffs(D, pdeg));
+    orc_multi_indices(D, pdeg, pex);
+    for (int i = 0; i < D; ++i) g[i] = 0.0;
+    for (int a = 0; a < d->n_poly; ++a) {
+        for (int i = 0; i < D; ++i) {
+            int ai = pex[a * D + i];
+            if (ai == 0) continue;
+            double term = d->poly_coef[a] * ai;
+            for (int k = 0; k < D; ++k) term *= pow(x[k], pex[a * D + k] - (k == i ? 1 : 0));
+            g[i] += term;
+        }
+    }
+    free(pex);
+}
+
+
 /* ------------------------------------------------------- fitted operators
  * Sec. 3.1 replaces the Taylor coefficients of the kernel about a cell-pair offset c by those of
  * a polynomial fitted to the kernel in the least-squares sense over the separations the pair can
@@ -446,8 +473,8 @@ static double centre(const orc_desc *d, int nl, int ci) {
 
 
 /* ------------------------------------------------------------------- rays
- * Rays x(t) = o + t r for t in [t0, t1] (Sec. 4, the integral-implicit layer: "Line to
- * polynomial" and ray2M).  A ray is cut into segments at the faces of the finest cells (the part
+ * Rays x(t) = o + t r for t in [t0, t1] (Sec. 6, the integral-implicit layer: "Line Integral"
+ * with line2poly of Sec. 5, "Line to polynomial", and "Line Integral JVP" with ray2M).  A ray is cut into segments at the faces of the finest cells (the part
  * outside the domain box is dropped); each segment lies in one cell, found from its midpoint by
  * the binning rule.  (3D only.) */
 typedef struct { const double *o, *r, *t0, *t1, *wt; int64_t n; } orc_rayset;
@@ -625,7 +652,7 @@ static int pipeline(const orc_desc *d,
         for (int b = 0; b < P; ++b) Mx[0][lin * P + b] += wt[i] * mono(&ix, b, pw);
     }
 
-    /* ---- ray2M (Sec. 4): every segment of a source ray adds its weight times line2taylor to the
+    /* ---- ray2M (Sec. 6, "Line Integral JVP"): every segment of a source ray adds its weight times line2taylor to the
      * moments of its cell, entry point taken relative to the cell centre */
     if (src_rays) {
         double *mt = (double *)malloc(sizeof(double) * P);
@@ -848,7 +875,7 @@ static int pipeline(const orc_desc *d,
         }
     }
 
-    /* ---- ray integrals (Sec. 4): each segment's cell series restricted to the line (line2poly),
+    /* ---- ray integrals (Sec. 6, "Line Integral"): each segment's cell series restricted to the line (line2poly),
      * integrated over the segment: int_0^s sum_m a_m x^m dx = sum_m a_m s^(m+1) / (m+1) */
     if (tgt_rays)
         for (int64_t q = 0; q < tgt_rays->n; ++q) {
@@ -893,7 +920,7 @@ int orc_transform(const orc_desc *d,
     return orc_transform_h(d, src, wt, n_src, src_cell, tgt, n_tgt, tgt_cell, sel, n_sel, val, grad, NULL, fault);
 }
 
-/* Ray integrals of the transform (Sec. 4, integral-implicit layer), rays given by origins o and
+/* Ray integrals of the transform (Sec. 6, integral-implicit layer), rays given by origins o and
  * directions r [n_ray][3] and parameter ranges [t0, t1] (clipped to the domain box):
  *   forward:  y_q = int_{t0}^{t1} f(o_q + t r_q) dt,  f the series of (src, wt)  (line2poly);
  *   backward: value (and gradient) at the targets of the transform whose sources are the rays with
@@ -930,5 +957,35 @@ int orc_direct(const orc_desc *d, const double *src, const double *wt, int64_t n
         }
         val[j] = acc;
     }
+    return 0;
+}
+
+/* Exact gradients of <ybar, y> for the direct sum y_m = sum_n psi(p_n - q_m) w_n of Eq. 1 (the dense
+ * form of Sec. 4.1's Jacobian vector product), at the selected sources n:
+ *   wbar_n = sum_m ybar_m psi(p_n - q_m),      pbar_n = w_n sum_m ybar_m (grad psi)(p_n - q_m).
+ * pbar may be NULL. */
+int orc_direct_grad(const orc_desc *d, const double *src, const double *wt, int64_t n_src,
+                    const double *tgt, const double *ybar, int64_t n_tgt, const int64_t *sel, int64_t n_sel,
+                    double *wbar, double *pbar) {
+    int D = d->dim;
+    if (n_sel < 0) n_sel = n_src;
+    #pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n_sel; ++j) {
+        int64_t si = sel ? sel[j] : j;
+        double acc = 0.0, ga[ORC_MAXD] = {0.0, 0.0, 0.0};
+        for (int64_t m = 0; m < n_tgt; ++m) {
+            double x[ORC_MAXD], g[ORC_MAXD];
+            for (int k = 0; k < D; ++k) x[k] = src[si * D + k] - tgt[m * D + k];
+            acc += kernel_value(d, x) * ybar[m];
+            if (pbar) {
+                kernel_grad(d, x, g);
+                for (int k = 0; k < D; ++k) ga[k] += g[k] * ybar[m];
+            }
+        }
+        wbar[j] = acc;
+        if (pbar)
+            for (int k = 0; k < D; ++k) pbar[j * D + k] = wt[si] * ga[k];
+    }
+    (void)n_src;
     return 0;
 }

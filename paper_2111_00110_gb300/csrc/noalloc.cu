@@ -10,16 +10,18 @@
 //
 // The array is part of the library image: every GPU that loads the library holds it
 // (kScratchBytes) until the process exits.  All calls share it, and it keeps the previous
-// call's contents; everything that must start from zero is cleared by the call itself.
-// Two calls whose work overlaps on the GPU (different streams, or different host threads)
-// race on the array and give wrong results: issue them on one stream, one after the other.
+// call's contents; everything that must start from zero is cleared by the call itself, and the
+// operator tables are rebuilt on the device by every call (a small kernel, FP64 arithmetic), so
+// no host memory is read after the call returns.  Two calls whose work overlaps on the GPU
+// (different streams, or different host threads) race on the array and give wrong results:
+// issue them on one stream, one after the other.
 //
-// The device address of the array is looked up once per device with cudaGetSymbolAddress
-// (host code cannot use the array's name as a device pointer); the first call on a device
-// does this set-up, so make the first call outside any CUDA stream capture.
+// Host code cannot use the array's name as a device pointer.  Every call asks the runtime for
+// the array's device address on the current device (cudaGetSymbolAddress; not a stream
+// operation), so the address is never stale, even after a device reset.  The first call on a
+// device also loads the library's device code there (set-up), so make the first call outside
+// any CUDA stream capture.
 #include <cmath>
-#include <cstring>
-#include <mutex>
 
 #include "fc2t2_internal.cuh"
 
@@ -55,43 +57,69 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-std::mutex g_na_mutex;                 // guards the host staging tables and the address cache
-void *g_na_addr[128] = {nullptr};      // device address of the scratch array, per device
-
-// host staging of the operator tables (static storage, no allocation)
-float h_dtab[kNaMaxLevels * kNaOffsets * kNaMaxPp];
-int h_start[kNaMaxPp + 1];
-int2 h_pairs[kNaMaxPairs];
-
-struct SmallIndex {
-    int D, rho, P;
-    int e[kNaMaxPp][3];
-    int deg[kNaMaxPp];
-    int index(int a0, int a1, int a2) const {
-        if (a0 < 0 || a1 < 0 || a2 < 0 || a0 + a1 + a2 > rho) return -1;
-        return D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
-    }
-};
-
-void small_index(int D, int rho, SmallIndex &ix) {
-    ix.D = D; ix.rho = rho; ix.P = ncoef(D, rho);
-    for (int a0 = 0; a0 <= rho; ++a0)
-        for (int a1 = 0; a0 + a1 <= rho; ++a1)
-            for (int a2 = 0; a0 + a1 + a2 <= rho; ++a2) {
+// Operator tables on the device, as a plan builds them on the host (the same definitions):
+//   dtab[l][o][k] = h_l^|k| d^k psi(o h_l),  psi = exp(-|x|^2 / (2 sigma^2)),  o in {-3..3}^D,
+// from the one-dimensional factors h^j g^(j)(x) (probabilists' Hermite recurrence in FP64), and
+// the CUDA-core M2L's pair lists: for every output k, the inputs b with |k| + |b| <= rho and the
+// index of k + b.  One block per (level, offset); block 0's thread 0 also writes the pair lists.
+__device__ int na_exponents(int D, int rho, int k, int e[3]) {
+    for (int d = 0; d <= rho; ++d)
+        for (int a0 = d; a0 >= 0; --a0)
+            for (int a1 = d - a0; a1 >= 0; --a1) {
+                const int a2 = d - a0 - a1;
                 if (D == 2 && a2) continue;
-                const int k = D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2);
-                ix.e[k][0] = a0; ix.e[k][1] = a1; ix.e[k][2] = a2; ix.deg[k] = a0 + a1 + a2;
+                if ((D == 2 ? gidx2(a0, a1) : gidx3(a0, a1, a2)) == k) {
+                    e[0] = a0; e[1] = a1; e[2] = a2;
+                    return d;
+                }
             }
+    e[0] = e[1] = e[2] = 0;
+    return -1;
 }
 
-// h^j g^(j)(x), g = exp(-x^2/(2 sigma^2)), probabilists' Hermite recurrence
-void gauss_1d(double sigma, double h, double x, int J, double *out) {
-    const double v = x / sigma, g = std::exp(-0.5 * v * v), r = -h / sigma;
-    double hem1 = 0.0, he = 1.0, f = 1.0;
-    for (int j = 0; j <= J; ++j) {
-        out[j] = f * he * g;
-        const double hn = v * he - j * hem1;
-        hem1 = he; he = hn; f *= r;
+__global__ void k_na_tables(float *dtab, int *start, int2 *pairs, int D, int rho, int Pp, int nofs, double sigma,
+                            double h0) {
+    const int l = blockIdx.x / nofs, o = blockIdx.x % nofs;
+    const int P = ncoef(D, rho);
+    const double h = h0 * (double)(1 << l);
+    for (int k = threadIdx.x; k < Pp; k += blockDim.x) {
+        float out = 0.0f;
+        if (k < P) {
+            int e[3];
+            na_exponents(D, rho, k, e);
+            double v = 1.0;
+            int r = o;
+            for (int d = 0; d < D; ++d) {
+                const double x = (double)(r % 7 - 3) * h;
+                r /= 7;
+                const double t = x / sigma, g = exp(-0.5 * t * t), f = -h / sigma;
+                double hem1 = 0.0, he = 1.0, fj = 1.0;     // He_j(t) and (-h/sigma)^j
+                for (int j = 0; j < e[d]; ++j) {
+                    const double hn = t * he - j * hem1;
+                    hem1 = he; he = hn; fj *= f;
+                }
+                v *= fj * he * g;
+            }
+            out = (float)v;
+        }
+        dtab[(size_t)blockIdx.x * Pp + k] = out;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int cnt = 0;
+        for (int a = 0; a < P; ++a) {
+            int ea[3];
+            const int da = na_exponents(D, rho, a, ea);
+            start[a] = cnt;
+            for (int b = 0; b < P; ++b) {
+                int eb[3];
+                const int db = na_exponents(D, rho, b, eb);
+                if (da + db > rho) continue;
+                const int kb = D == 2 ? gidx2(ea[0] + eb[0], ea[1] + eb[1])
+                                      : gidx3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
+                pairs[cnt++] = make_int2(b, kb);
+            }
+        }
+        start[P] = cnt;
     }
 }
 
@@ -120,6 +148,10 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
         return set_error(FC2T2_ERR_INVALID_ARG, "domain must satisfy lo < hi");
     if (desc->channels != 1 || desc->m2l != FC2T2_M2L_FP32 || desc->fit != 0)
         return set_error(FC2T2_ERR_UNSUPPORTED, "the allocation-free path supports one channel, FP32 M2L, Taylor operators");
+    if (desc->check_domain != 0)
+        return set_error(FC2T2_ERR_UNSUPPORTED,
+                         "the allocation-free path does not check the domain (points outside clamp to the edge cells); "
+                         "set check_domain = 0 or use a plan");
     if (desc->grid < 4 || (desc->grid & (desc->grid - 1)))
         return set_error(FC2T2_ERR_INVALID_ARG, "grid must be a power of two >= 4");
     int64_t cells = 1;
@@ -136,18 +168,11 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     if (!q || !y || (N > 0 && (!p || !w))) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
     cudaStream_t s = (cudaStream_t)stream;
 
-    std::lock_guard<std::mutex> lock(g_na_mutex);
-    int dev = 0;
-    fc2t2_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    // the array's device address on the current device (looked up on every call)
+    void *addr = nullptr;
+    fc2t2_status st = check_cuda(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress");
     if (st != FC2T2_OK) return st;
-    if (dev < 0 || dev >= 128) return set_error(FC2T2_ERR_UNSUPPORTED, "device ordinal too large");
-    if (!g_na_addr[dev]) {
-        void *addr = nullptr;
-        st = check_cuda(cudaGetSymbolAddress(&addr, g_noalloc_scratch), "cudaGetSymbolAddress");
-        if (st != FC2T2_OK) return st;
-        g_na_addr[dev] = addr;
-    }
-    unsigned char *base = static_cast<unsigned char *>(g_na_addr[dev]);
+    unsigned char *base = static_cast<unsigned char *>(addr);
 
     // a plan on the stack whose device pointers all point into the scratch array
     fc2t2_plan_s pl;
@@ -196,43 +221,11 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     }
     if (off > kScratchBytes) return set_error(FC2T2_ERR_UNSUPPORTED, "scratch layout exceeds the array");
 
-    // operator tables (the same definitions as a plan's), staged in static host memory
-    SmallIndex ix;
-    small_index(pl.D, pl.rho, ix);
-    const int P = pl.P, Pp = pl.Pp, D = pl.D, nofs = D == 3 ? 343 : 49;
-    std::memset(h_dtab, 0, sizeof(float) * (size_t)pl.nlev * nofs * Pp);
-    for (int l = 0; l < pl.nlev; ++l) {
-        const double h = pl.lev[l].h;
-        for (int o = 0; o < nofs; ++o) {
-            double g[3][kNaMaxOrder + 1];
-            int r = o;
-            for (int d = 0; d < D; ++d) { gauss_1d(desc->sigma, h, (double)(r % 7 - 3) * h, pl.rho, g[d]); r /= 7; }
-            for (int k = 0; k < P; ++k) {
-                double v = 1.0;
-                for (int d = 0; d < D; ++d) v *= g[d][ix.e[k][d]];
-                h_dtab[((size_t)l * nofs + o) * Pp + k] = (float)v;
-            }
-        }
-    }
-    int cnt = 0;   // the M2L pair lists, as a plan's
-    for (int a = 0; a < P; ++a) {
-        h_start[a] = cnt;
-        for (int b = 0; b < P; ++b) {
-            if (ix.deg[a] + ix.deg[b] > pl.rho) continue;
-            h_pairs[cnt++] = make_int2(b, ix.index(ix.e[a][0] + ix.e[b][0], ix.e[a][1] + ix.e[b][1],
-                                                   ix.e[a][2] + ix.e[b][2]));
-        }
-    }
-    h_start[P] = cnt;
-
-    // pageable host-to-device copies return once the host data has been staged
-    struct Up { void *dst; const void *src; size_t bytes; } ups[] = {
-        {pl.d_dtab, h_dtab, sizeof(float) * (size_t)pl.nlev * nofs * Pp},
-        {pl.d_m2l_start, h_start, sizeof(int) * (size_t)(P + 1)}, {pl.d_m2l_pairs, h_pairs, sizeof(int2) * (size_t)cnt},
-    };
-    for (const Up &u : ups)
-        if ((st = check_cuda(cudaMemcpyAsync(u.dst, u.src, u.bytes, cudaMemcpyHostToDevice, s), "upload tables")) != FC2T2_OK)
-            return st;
+    // operator tables, built on the device into the scratch array
+    const int nofs = pl.D == 3 ? 343 : 49;
+    k_na_tables<<<pl.nlev * nofs, 64, 0, s>>>(pl.d_dtab, pl.d_m2l_start, pl.d_m2l_pairs, pl.D, pl.rho, pl.Pp, nofs,
+                                              desc->sigma, pl.lev[0].h);
+    if ((st = check_cuda(cudaGetLastError(), "operator tables")) != FC2T2_OK) return st;
     if ((st = check_cuda(cudaMemsetAsync(pl.d_flags, 0, 4 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
     if (N == 0) return check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y");
 

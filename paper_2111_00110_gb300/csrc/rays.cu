@@ -1,4 +1,4 @@
-// Ray integrals of the transform (Sec. 4, the integral-implicit layer): for rays x(t) = o + t r,
+// Ray integrals of the transform (Sec. 6, the integral-implicit layer): for rays x(t) = o + t r,
 // t in [t0, t1],
 //     forward   y_q = int f(o_q + t r_q) dt          (f: the finest-level local series)
 //     adjoint   the rays as sources with weights ybar_q (ray2M): every segment of a ray inside a

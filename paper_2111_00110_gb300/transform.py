@@ -172,7 +172,7 @@ class Plan:
 
     def ray_forward(self, p: torch.Tensor, w: torch.Tensor, rays: torch.Tensor) -> torch.Tensor:
         """Integrals of the series of (p, w) along rays [R, 8] = (origin, direction, t0, t1):
-        y[c, q] = int_{t0}^{t1} f_c(o_q + t r_q) dt (Sec. 4, the integral-implicit layer)."""
+        y[c, q] = int_{t0}^{t1} f_c(o_q + t r_q) dt (Sec. 6, the integral-implicit layer)."""
         N, R = p.shape[0], rays.shape[0]
         _check_tensor(p, "p", (N, self.dim))
         _check_tensor(w, "w", self._chan_shape(w, N))
@@ -199,7 +199,7 @@ class Plan:
 
 
 class FC2T2RayFunction(torch.autograd.Function):
-    """y = integrals of f(.; p, w) along fixed rays, with the adjoints of Sec. 4 (ray2M)."""
+    """y = integrals of f(.; p, w) along fixed rays, with the adjoints of Sec. 6 (ray2M)."""
 
     @staticmethod
     def forward(ctx, p, w, rays, plan: "Plan"):
@@ -219,7 +219,7 @@ class FC2T2RayFunction(torch.autograd.Function):
 
 
 def fc2t2_rays(p: torch.Tensor, w: torch.Tensor, rays: torch.Tensor, plan: "Plan") -> torch.Tensor:
-    """Differentiable ray integrals of the transform (Sec. 4)."""
+    """Differentiable ray integrals of the transform (Sec. 6)."""
     return FC2T2RayFunction.apply(p, w, rays, plan)
 
 

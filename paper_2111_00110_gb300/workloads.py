@@ -6,7 +6,7 @@ with ``numpy.random.default_rng(seed)`` in the order (p, w, q) and returns float
 (the precision the transform consumes), plus the transform parameters.
 
 The paper's own workloads (signed-distance fitting with 8m sources / 10m targets, and
-radiance-field rays; Sec. 3.3 and Sec. 4.3) need meshes and image datasets that are not
+radiance-field rays; Sec. 4.3 and Sec. 6.3) need meshes and image datasets that are not
 available; these synthetic sets reproduce their shapes and sizes:
 
 * ``uniform2d``   -- 2D, N = M = 4096 uniform in [0,1)^2, w ~ N(0,1), sigma 0.05,

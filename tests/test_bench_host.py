@@ -37,6 +37,15 @@ def test_separable_bytes_match_enumeration(order, levels, grid):
     assert bench.separable_bytes(P, levels, grid) == want
 
 
+def test_m2l_algorithmic_bytes_at_the_bench_size():
+    """Moments read once and locals written once over the five levels of 64^3 at order 6:
+    299,584 cells x 84 values x 4 bytes x 2."""
+    import bench
+    cells = sum((64 >> l) ** 3 for l in range(5))
+    assert cells == 299_584
+    assert bench.m2l_algorithmic_bytes(84, 5, 64) == cells * 84 * 4 * 2 == 201_320_448
+
+
 def test_separable_bytes_at_the_bench_size():
     # 64^3, order 6, five levels: 1.334 GB per transform (2.667 GB per step of two transforms)
     assert bench.separable_bytes(84, 5, 64) == 1_333_721_088

@@ -1,4 +1,4 @@
-"""GPU parity of the ray integrals (Sec. 4, the integral-implicit layer): integrals of the series
+"""GPU parity of the ray integrals (Sec. 6, the integral-implicit layer): integrals of the series
 along rays (forward) and their adjoint (the rays inserted as sources, ray2M), against the FP64
 oracle, which cuts the rays at the same faces but integrates each segment with the paper's
 binomial line2poly / line2taylor formulas.

@@ -12,6 +12,9 @@
 * adjoint identity     -- Sec. 4.1: the backward transform is the transpose;
 * finite differences   -- wbar and pbar (Sec. 4.1) against central differences of the
                           forward map with the binning held fixed;
+* dense gradient       -- the exact gradient of the direct sum against its own central
+                          differences, and the transform's gradients against it (agreement
+                          to truncation error, falling with the order);
 * truncation decay     -- error against the exact sum decreases with the order;
 * special cases        -- one source / one target closed form, empty inputs, linearity,
                           permutation invariance;
@@ -178,7 +181,8 @@ def test_polynomial_derivatives_vs_sympy(dim):
         assert np.max(np.abs(got - ref)) <= 1e-12 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("dim,grid,order", [(2, 8, 3), (2, 16, 4), (3, 8, 3), (3, 16, 2), (2, 32, 2)])
+@pytest.mark.parametrize("dim,grid,order", [(2, 8, 3), (2, 16, 4), (3, 8, 3), (3, 16, 2), (2, 32, 2),
+                                            (3, 16, 6), (3, 8, 8)])
 def test_per_pair_identity(dim, grid, order):
     p, w, q = small_inputs(10 + dim + grid + order, dim, 60, 50)
     sigma = 0.15 if grid == 8 else 0.08
@@ -266,6 +270,59 @@ def test_gradients_vs_central_differences(dim):
             scale = abs(pbar[n, i]) + 1e-3 * np.sqrt(L0) / d.sigma
             assert abs(vals[0] - pbar[n, i]) <= 2e-3 * scale
             assert abs(vals[1] - pbar[n, i]) <= 2e-5 * scale
+
+
+@pytest.mark.parametrize("kind", ["gaussian", "poly"])
+@pytest.mark.parametrize("dim", [2, 3])
+def test_direct_gradient_vs_central_differences(kind, dim):
+    """The dense gradient of <ybar, y> for the exact sum (Sec. 4.1 applied to Eq. 1) against
+    central differences of the exact sum itself: exact to rounding in w (the sum is linear in w),
+    second order in eps in p.  The polynomial is odd, so a sign slip in the gradient fails it."""
+    p, w, q = small_inputs(200 + dim, dim, 25, 35)
+    if kind == "gaussian":
+        d = oracle.OracleDesc(dim=dim, grid=8, order=4, sigma=0.1)
+    else:
+        terms = {m: v for m, v in POLYS_3D["odd_mixed"].items() if dim == 3 or m[2] == 0}
+        d = oracle.OracleDesc(dim=dim, grid=8, order=4, kernel="poly", poly_coef=poly_coef(terms, dim, 3))
+    ybar = np.random.default_rng(201).standard_normal(q.shape[0])
+    sel = np.array([0, 7, 13, 24])
+    wbar, pbar = oracle.direct_grad(d, p, w, q, ybar, sel=sel)
+    full_w, full_p = oracle.direct_grad(d, p, w, q, ybar)
+    assert np.array_equal(full_w[sel], wbar) and np.array_equal(full_p[sel], pbar)
+    L = lambda pp, ww: float(ybar @ oracle.direct(d, pp, ww, q))
+    scale = np.abs(ybar) @ np.abs(oracle.direct(d, p, np.abs(w), q)) + 1e-300
+    for j, n in enumerate(sel):
+        wp, wm = w.copy(), w.copy()
+        wp[n] += 1e-3
+        wm[n] -= 1e-3
+        assert abs((L(p, wp) - L(p, wm)) / 2e-3 - wbar[j]) <= 1e-10 * scale
+        for i in range(dim):
+            for eps, tol in ((1e-4, 1e-5), (1e-5, 1e-7)):
+                pp, pm = p.copy(), p.copy()
+                pp[n, i] += eps
+                pm[n, i] -= eps
+                fd = (L(pp, w) - L(pm, w)) / (2 * eps)
+                assert abs(fd - pbar[j, i]) <= tol * (np.abs(full_p).max() + 1e-300), (n, i, eps)
+
+
+def test_transform_gradients_approach_the_dense_gradient():
+    """wbar and pbar of the transform (Sec. 4.1) against the exact gradient of the direct sum at
+    the same cotangent: they agree to the truncation error of the series, which falls with the
+    order (the 2D 32 x 32 workload, sigma 0.05)."""
+    wl = workloads.uniform2d()
+    p, w, q = (a.astype(np.float64) for a in (wl.p, wl.w, wl.q))
+    ybar = np.random.default_rng(202).standard_normal(q.shape[0])
+    d = oracle.OracleDesc(dim=2, grid=wl.grid, order=2, sigma=wl.sigma)
+    wd, pd = oracle.direct_grad(d, p, w, q, ybar)
+    ew, ep = [], []
+    for order in (2, 4, 6, 8):
+        d.order = order
+        wb, pb = oracle.backward(d, p, w, q, ybar)
+        ew.append(rel(wb, wd))
+        ep.append(rel(pb, pd))
+    assert all(a > b for a, b in zip(ew, ew[1:])), ew
+    assert all(a > b for a, b in zip(ep, ep[1:])), ep
+    assert ew[1] <= 2e-2 and ep[1] <= 8e-2, (ew, ep)
 
 
 @pytest.mark.parametrize("dim", [2, 3])
@@ -442,7 +499,7 @@ def test_each_planted_mistake_fails_a_pin(fault):
     assert any(caught), fault
 
 
-# ---------------------------------------------------------------- rays (Sec. 4, integral layer)
+# ---------------------------------------------------------------- rays (Sec. 6, integral layer)
 
 def _clip(o, r, t0, t1, lo=0.0, hi=1.0):
     """Parameter range of o + t r inside [lo, hi)^3 within [t0, t1] (slab method), or None."""

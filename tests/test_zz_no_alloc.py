@@ -1,15 +1,19 @@
-"""The allocation-free forward transform (fc2t2_forward_noalloc) against the planned one.
+"""The allocation-free forward transform (fc2t2_forward_noalloc) against the planned one and the
+oracle.
 
 fc2t2_forward_noalloc serves callers that cannot call cudaMalloc when they need a transform
 (for example inside a framework that owns all device memory, or a real-time loop that must
 not allocate); it keeps its intermediates in a static device array of the library.  This file
 is collected last so that a run stopping at the first failure has already run every other test.
+
+Tolerance: the FP32 bar of the parity tests (relative L2 <= 1e-5).
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2111_00110_gb300 import workloads
 
 pytestmark = pytest.mark.gpu
@@ -40,12 +44,16 @@ def desc_for(wl):
     return d
 
 
-def noalloc_forward(lib, wl, stream):
-    p, w, q = (torch.from_numpy(a).cuda() for a in (wl.p, wl.w, wl.q))
-    y = torch.full((wl.M,), float("nan"), device="cuda")
-    d = desc_for(wl)
-    st = lib.fc2t2_forward_noalloc(ctypes.byref(d), stream, p.data_ptr(), w.data_ptr(), wl.N,
-                                   q.data_ptr(), wl.M, y.data_ptr())
+def noalloc_forward(lib, wl, stream, n_src=None):
+    """One call on `stream` (a torch.cuda.Stream or None for the current one)."""
+    n = wl.N if n_src is None else n_src
+    s = torch.cuda.current_stream() if stream is None else stream
+    with torch.cuda.stream(s):
+        p, w, q = (torch.from_numpy(a).cuda() for a in (wl.p, wl.w, wl.q))
+        y = torch.full((wl.M,), float("nan"), device="cuda")
+        d = desc_for(wl)
+        st = lib.fc2t2_forward_noalloc(ctypes.byref(d), s.cuda_stream, p.data_ptr(), w.data_ptr(), n,
+                                       q.data_ptr(), wl.M, y.data_ptr())
     assert st == 0, st
     torch.cuda.synchronize()
     return y.cpu().numpy()
@@ -62,16 +70,43 @@ def planned_forward(wl):
     return out
 
 
+def oracle_forward(wl, sel=None):
+    d = oracle.OracleDesc(dim=wl.dim, grid=wl.grid, order=wl.order, sigma=wl.sigma)
+    f = lambda a: np.asarray(a, dtype=np.float64)
+    return oracle.forward(d, f(wl.p), f(wl.w), f(wl.q), sel=sel)
+
+
 def test_noalloc_matches_planned_forward_twice(lib):
-    stream = torch.cuda.current_stream().cuda_stream
     # two different problems back to back: the shared array must not carry state over
     first = workloads.uniform(901, 3, 20000, 15000, 16, 4, 0.06)
     second = workloads.uniform(902, 2, 30000, 25000, 64, 3, 0.03)
     for wl in (first, second):
-        y_na = noalloc_forward(lib, wl, stream)
+        y_na = noalloc_forward(lib, wl, None)
         y_pl = planned_forward(wl)
         assert np.all(np.isfinite(y_na))
         assert rel_l2(y_na, y_pl) <= REL_L2
+        assert rel_l2(y_na, oracle_forward(wl)) <= REL_L2
+
+
+@pytest.mark.parametrize("dim,grid", [(3, 16), (2, 64)])
+def test_noalloc_at_its_limits(lib, dim, grid):
+    """N = M = 65536 (the largest sort), order 4 (the largest rows) and 4096 finest cells; 64^2
+    has five levels, the most the array holds.  Run on a stream other than the current one, and
+    checked against the oracle at 4096 seeded queries."""
+    wl = workloads.uniform(904 + dim, dim, 65536, 65536, grid, 4, 1.3 / grid)
+    side = torch.cuda.Stream()
+    y_na = noalloc_forward(lib, wl, side)
+    sel = np.sort(np.random.default_rng(905).choice(wl.M, size=4096, replace=False))
+    assert np.all(np.isfinite(y_na))
+    assert rel_l2(y_na[sel], oracle_forward(wl, sel=sel)) <= REL_L2
+    assert rel_l2(y_na, planned_forward(wl)) <= REL_L2
+
+
+def test_noalloc_without_sources_gives_zero(lib):
+    wl = workloads.uniform(906, 3, 1000, 3000, 16, 4, 0.06)
+    noalloc_forward(lib, wl, None)                    # leaves nonzero coefficients in the array
+    y = noalloc_forward(lib, wl, None, n_src=0)
+    assert np.all(y == 0.0)
 
 
 def test_noalloc_rejects_requests_beyond_its_limits(lib):
@@ -86,3 +121,5 @@ def test_noalloc_rejects_requests_beyond_its_limits(lib):
     assert lib.fc2t2_forward_noalloc(ctypes.byref(d), None, 1, 1, wl.N, 1, wl.M, 1) == 1
     d.order = 4
     assert lib.fc2t2_forward_noalloc(ctypes.byref(d), None, 1, 1, 70000, 1, wl.M, 1) == 1
+    d.check_domain = 1                                             # never reported on this path
+    assert lib.fc2t2_forward_noalloc(ctypes.byref(d), None, 1, 1, wl.N, 1, wl.M, 1) == 2
