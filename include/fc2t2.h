@@ -161,8 +161,9 @@ FC2T2_API fc2t2_status fc2t2_direct(const fc2t2_plan_desc *desc, void *stream, c
                                     int64_t N, const float *q, int64_t M, float *y);
 
 /* Synchronise `stream` and report the device-side conditions raised on `plan`: TIMEOUT if a
- * bounded device-side wait of the tensor-core M2L gave up in any call since the last check (the
- * outputs of that call are then incomplete; the condition is cleared by this check), DOMAIN if
+ * bounded device-side wait (the staging of P2M, L2P or the M2L, or the tensor-core M2L's pipeline;
+ * every such wait gives up after 0.2 s) gave up in any call since the last check (the outputs of
+ * that call are then incomplete; the condition is cleared by this check), DOMAIN if
  * check_domain is set and the last call saw a point outside the domain.  Forward and backward
  * make the same check themselves when check_domain is set.  Errors: INVALID_ARG, CUDA, and the
  * two conditions above. */

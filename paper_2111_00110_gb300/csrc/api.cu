@@ -268,8 +268,8 @@ static void destroy(fc2t2_plan_s *pl) {
     if (pl->run) cudaStreamDestroy(pl->run);
     if (pl->ev_run_fork) cudaEventDestroy(pl->ev_run_fork);
     if (pl->ev_run_done) cudaEventDestroy(pl->ev_run_done);
-    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab); cudaFree(pl->d_m2l_start);
-    cudaFree(pl->d_m2l_pairs); cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
+    cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab);
+    cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
     cudaFree(pl->d_mma_ops);
     for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
     cudaFree(pl->sep.d_t);
@@ -303,28 +303,9 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
             }
         }
     }
-    // M2L pair lists of the CUDA-core form: for every output k, the b with |k| + |b| <= rho and
-    // the index of k + b
-    std::vector<int> m2l_start(P + 1);
-    std::vector<int2> m2l_pairs;
-    for (int a = 0; a < P; ++a) {
-        m2l_start[a] = (int)m2l_pairs.size();
-        for (int b = 0; b < P; ++b) {
-            if (ix.deg[a] + ix.deg[b] > rho) continue;
-            const int kb = ix.index(ix.e[3 * a] + ix.e[3 * b], ix.e[3 * a + 1] + ix.e[3 * b + 1],
-                                    ix.e[3 * a + 2] + ix.e[3 * b + 2]);
-            m2l_pairs.push_back(make_int2(b, kb));
-        }
-    }
-    m2l_start[P] = (int)m2l_pairs.size();
-
     fc2t2_status st;
     if ((st = dev_alloc(&pl->d_dtab, dtab.size(), "derivative tables")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_m2l_start, m2l_start.size(), "m2l index")) != FC2T2_OK) return st;
-    if ((st = dev_alloc(&pl->d_m2l_pairs, m2l_pairs.size(), "m2l pairs")) != FC2T2_OK) return st;
     if ((st = upload(pl->d_dtab, dtab, "upload derivative tables")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_m2l_start, m2l_start, "upload m2l index")) != FC2T2_OK) return st;
-    if ((st = upload(pl->d_m2l_pairs, m2l_pairs, "upload m2l pairs")) != FC2T2_OK) return st;
     // tensor-core operator images (3D; other dimensions keep the CUDA-core M2L)
     if (pl->desc.m2l == FC2T2_M2L_SEPARABLE) return build_sep(pl, dtab64);
     if (pl->desc.m2l != FC2T2_M2L_FP32 && D == 3)
@@ -372,8 +353,9 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     return FC2T2_OK;
 }
 
-// flags[0]: domain (cleared by every call); flags[2]: a tensor-core wait gave up (sticky until
-// fc2t2_plan_check)
+// flags[0]: domain (cleared by every call); flags[2]: a bounded device-side wait gave up (sticky
+// until fc2t2_plan_check; bit 2048: the CUDA-core M2L's staging, 1024 / 512: P2M's / L2P's, the
+// low bits: the tensor-core M2L's pipeline)
 static fc2t2_status read_flags(fc2t2_plan_s *pl, cudaStream_t s, bool clear_sticky) {
     int flags[3] = {0, 0, 0};
     fc2t2_status st = check_cuda(cudaMemcpyAsync(flags, pl->d_flags, 3 * sizeof(int), cudaMemcpyDeviceToHost, s),
@@ -384,7 +366,8 @@ static fc2t2_status read_flags(fc2t2_plan_s *pl, cudaStream_t s, bool clear_stic
         return st;
     st = check_cuda(cudaStreamSynchronize(s), "synchronise");
     if (st != FC2T2_OK) return st;
-    if (flags[2]) return set_error(FC2T2_ERR_TIMEOUT, "a device-side wait of the tensor-core M2L gave up");
+    if (flags[2])
+        return set_error(FC2T2_ERR_TIMEOUT, "a bounded device-side wait gave up (code " + std::to_string(flags[2]) + ")");
     if (pl->desc.check_domain && (flags[0] & 1)) return set_error(FC2T2_ERR_DOMAIN, "a point lies outside [lo, hi)^dim");
     return FC2T2_OK;
 }

@@ -160,8 +160,6 @@ struct fc2t2_plan_s {
     cudaEvent_t ev_run_fork = nullptr, ev_run_done = nullptr;
     uint64_t batch_mark = 0;
     float *d_dtab = nullptr;      // [nlev][7^D][Pp]  scaled kernel derivatives
-    int *d_m2l_start = nullptr;   // [P+1]  per k: pairs (b, k+b) with |b| <= rho-|k|
-    int2 *d_m2l_pairs = nullptr;
     int *d_scan_tmp = nullptr;    // block sums of the prefix scan
     int64_t scan_tmp_len = 0;
     int *d_flags = nullptr;       // [4] device error flags

@@ -36,7 +36,6 @@ constexpr int kNaMaxPp = 36;
 constexpr int kNaMaxLevels = 5;            // 64^2: 64, 32, 16, 8, 4
 constexpr int64_t kNaMaxCellsAllLevels = kNaMaxCells * 4 / 3 + 16;
 constexpr int kNaOffsets = 343;            // 7^3 cell offsets
-constexpr int kNaMaxPairs = 35 * 35;
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -46,7 +45,6 @@ constexpr size_t kSortBytes =
 constexpr size_t kScratchBytes =
     2 * align256(sizeof(float) * kNaMaxCellsAllLevels * kNaMaxPp) +                  // M, L
     align256(sizeof(float) * kNaMaxLevels * kNaOffsets * kNaMaxPp) +                 // dtab
-    align256(sizeof(int) * (kNaMaxPp + 1)) + align256(sizeof(int2) * kNaMaxPairs) +  // M2L pairs
     align256(sizeof(int) * 64) + align256(sizeof(int) * 4) +                         // scan, flags
     2 * kSortBytes;
 
@@ -57,11 +55,10 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 namespace {
 
-// Operator tables on the device, as a plan builds them on the host (the same definitions):
+// Operator table on the device, as a plan builds it on the host (the same definition):
 //   dtab[l][o][k] = h_l^|k| d^k psi(o h_l),  psi = exp(-|x|^2 / (2 sigma^2)),  o in {-3..3}^D,
-// from the one-dimensional factors h^j g^(j)(x) (probabilists' Hermite recurrence in FP64), and
-// the CUDA-core M2L's pair lists: for every output k, the inputs b with |k| + |b| <= rho and the
-// index of k + b.  One block per (level, offset); block 0's thread 0 also writes the pair lists.
+// from the one-dimensional factors h^j g^(j)(x) (probabilists' Hermite recurrence in FP64).
+// One block per (level, offset).
 __device__ int na_exponents(int D, int rho, int k, int e[3]) {
     for (int d = 0; d <= rho; ++d)
         for (int a0 = d; a0 >= 0; --a0)
@@ -77,8 +74,7 @@ __device__ int na_exponents(int D, int rho, int k, int e[3]) {
     return -1;
 }
 
-__global__ void k_na_tables(float *dtab, int *start, int2 *pairs, int D, int rho, int Pp, int nofs, double sigma,
-                            double h0) {
+__global__ void k_na_tables(float *dtab, int D, int rho, int Pp, int nofs, double sigma, double h0) {
     const int l = blockIdx.x / nofs, o = blockIdx.x % nofs;
     const int P = ncoef(D, rho);
     const double h = h0 * (double)(1 << l);
@@ -103,23 +99,6 @@ __global__ void k_na_tables(float *dtab, int *start, int2 *pairs, int D, int rho
             out = (float)v;
         }
         dtab[(size_t)blockIdx.x * Pp + k] = out;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int cnt = 0;
-        for (int a = 0; a < P; ++a) {
-            int ea[3];
-            const int da = na_exponents(D, rho, a, ea);
-            start[a] = cnt;
-            for (int b = 0; b < P; ++b) {
-                int eb[3];
-                const int db = na_exponents(D, rho, b, eb);
-                if (da + db > rho) continue;
-                const int kb = D == 2 ? gidx2(ea[0] + eb[0], ea[1] + eb[1])
-                                      : gidx3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
-                pairs[cnt++] = make_int2(b, kb);
-            }
-        }
-        start[P] = cnt;
     }
 }
 
@@ -205,8 +184,6 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     pl.d_M = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
     pl.d_L = carve<float>(base, off, (size_t)kNaMaxCellsAllLevels * kNaMaxPp);
     pl.d_dtab = carve<float>(base, off, (size_t)kNaMaxLevels * kNaOffsets * kNaMaxPp);
-    pl.d_m2l_start = carve<int>(base, off, kNaMaxPp + 1);
-    pl.d_m2l_pairs = carve<int2>(base, off, kNaMaxPairs);
     pl.d_scan_tmp = carve<int>(base, off, 64);
     pl.d_flags = carve<int>(base, off, 4);
     SortWork *sorts[2] = {&pl.src, &pl.qry};
@@ -221,10 +198,9 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     }
     if (off > kScratchBytes) return set_error(FC2T2_ERR_UNSUPPORTED, "scratch layout exceeds the array");
 
-    // operator tables, built on the device into the scratch array
+    // operator table, built on the device into the scratch array
     const int nofs = pl.D == 3 ? 343 : 49;
-    k_na_tables<<<pl.nlev * nofs, 64, 0, s>>>(pl.d_dtab, pl.d_m2l_start, pl.d_m2l_pairs, pl.D, pl.rho, pl.Pp, nofs,
-                                              desc->sigma, pl.lev[0].h);
+    k_na_tables<<<pl.nlev * nofs, 64, 0, s>>>(pl.d_dtab, pl.D, pl.rho, pl.Pp, nofs, desc->sigma, pl.lev[0].h);
     if ((st = check_cuda(cudaGetLastError(), "operator tables")) != FC2T2_OK) return st;
     if ((st = check_cuda(cudaMemsetAsync(pl.d_flags, 0, 4 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
     if (N == 0) return check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y");

@@ -1,19 +1,32 @@
 // M2M / L2L dispatch (the kernels are the register forms of shift_reg.cu) and the CUDA-core M2L
-// (Sec. 3).
+// (Sec. 3): the direct form, for any kernel (Gaussian, polynomial, least-squares fitted
+// operators), 2D and 3D.
 //
-// M2L on the CUDA cores: target cells of one parity class and one output index k per
-// block, so the interaction window (Sec. 3: the 6^D parity-dependent window, minus the
-// 3^D hole above the finest level) and the operator rows are uniform across a warp.
-//     Lt(k) = (-1)^|k| sum_{o in window} sum_{|b| <= rho-|k|} Dt[o](k+b) Mt[t+o](b)
+//     Lt[t](k) = (-1)^|k| sum_{o in window(t)} sum_{|b| <= rho-|k|} Dt[o](k+b) Mt[t+o](b)
+//
+// The window of target cell t is [-2, 3] per dimension where t is even and [-3, 2] where it is
+// odd (Sec. 3: the children of the parent's neighbours), minus the 3^D hole above the finest
+// level.  Split targets and sources into parity classes, t = 2a + s and t + o = 2(a + delta) + s'
+// per dimension: then o = 2 delta + s' - s, and as s' runs over the 2^D source classes and delta
+// over {-1, 0, 1}^D, o runs over the target's window exactly once.  So a CTA that owns a box of
+// targets of one class stages, for one source class at a time, the moment rows of the sources
+// at subgrid positions box + {-1, 0, 1}^D -- one copy serves all 3^D offsets that reach into it
+// (a row-address shift per offset) -- together with the 3^D derivative rows Dt[o] of those
+// offsets.  A thread owns one target and a compile-time range of output indices k: it loads an
+// offset's derivative row into registers once (a broadcast read) and then, for every input b,
+// one moment value that feeds all its outputs k with |k| + |b| <= rho.  Every index is known at
+// compile time, so the inner work is a straight run of FMAs.
+//
+// Staging is by bulk asynchronous copies (one per row, completing on an mbarrier with a bounded
+// wait); rows outside the grid are zero-filled.  The rows are stored at a pitch of an odd number
+// of 16-byte units, so the 16-byte shared loads of eight neighbouring targets hit distinct banks.
+#include <utility>
+
 #include "dispatch.cuh"
 #include "fc2t2_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace fc2t2 {
-
-__device__ __forceinline__ void unravel_cell(int64_t lin, int n, int D, int (&c)[3]) {
-    c[0] = c[1] = c[2] = 0;
-    for (int d = 0; d < D; ++d) { c[d] = (int)(lin % n); lin /= n; }
-}
 
 // M2M (level l -> l + 1) and L2L (level l + 1 -> l): the register kernels cover every dimension
 // and order a plan accepts.
@@ -27,78 +40,294 @@ cudaError_t launch_l2l(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     return launch_l2l_reg(pl, s, level, err) ? err : cudaErrorInvalidValue;
 }
 
-constexpr int kM2LThreads = 128;
+namespace {
 
-__global__ void __launch_bounds__(kM2LThreads) k_m2l_simple(
-    const float *__restrict__ M, float *__restrict__ L, int nl, int D, int Pp, int finest,
-    const float *__restrict__ dtab, const int *__restrict__ pstart, const int2 *__restrict__ pairs) {
-    const int k = blockIdx.y;
-    const int half = nl >> 1;
-    int64_t Gh = 1;
-    for (int d = 0; d < D; ++d) Gh *= half;
-    const int64_t nbp = (Gh + kM2LThreads - 1) / kM2LThreads;
-    const int pi = (int)(blockIdx.x / nbp);
-    const int64_t a = (int64_t)(blockIdx.x % nbp) * kM2LThreads + threadIdx.x;
-    if (a >= Gh) return;
-    int ac[3];
-    unravel_cell(a, half, D, ac);
-    int t[3] = {0, 0, 0}, lo[3] = {0, 0, 0}, hiw[3] = {0, 0, 0};
-    for (int d = 0; d < D; ++d) {
-        t[d] = 2 * ac[d] + ((pi >> d) & 1);
-        lo[d] = (t[d] & 1) ? -3 : -2;   // window [-3,+2] for odd, [-2,+3] for even indices
-        hiw[d] = lo[d] + 5;
-    }
-    const int nz = (D == 3) ? nl : 1;
-    const int e0 = pstart[k], e1 = pstart[k + 1];
-    float acc = 0.0f;
-    for (int oz = lo[2]; oz <= hiw[2]; ++oz) {
-        const int sz = t[2] + oz;
-        if (sz < 0 || sz >= nz) continue;
-        for (int oy = lo[1]; oy <= hiw[1]; ++oy) {
-            const int sy = t[1] + oy;
-            if (sy < 0 || sy >= nl) continue;
-            for (int ox = lo[0]; ox <= hiw[0]; ++ox) {
-                const int sx = t[0] + ox;
-                if (sx < 0 || sx >= nl) continue;
-                // the hole: interactions within one cell are resolved at the finer level
-                if (!finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1)
-                    continue;
-                const int olin = (ox + 3) + 7 * (oy + 3) + (D == 3 ? 49 * (oz + 3) : 0);
-                const int64_t slin = sx + (int64_t)nl * (sy + (int64_t)nl * sz);
-                const float *Do = dtab + (int64_t)olin * Pp;
-                const float *Ms = M + slin * Pp;
-                for (int e = e0; e < e1; ++e) {
-                    const int2 pr = pairs[e];
-                    acc = fmaf(__ldg(Do + pr.y), __ldg(Ms + pr.x), acc);
-                }
-            }
-        }
-    }
-    int deg = 0;
-    while (((D == 2) ? (deg + 1) * (deg + 2) / 2 : (deg + 1) * (deg + 2) * (deg + 3) / 6) <= k) ++deg;
-    const int64_t tlin = t[0] + (int64_t)nl * (t[1] + (int64_t)nl * t[2]);
-    L[tlin * Pp + k] = (deg & 1) ? -acc : acc;
+constexpr int kDirThreads = 256;
+
+// Output ranges per thread: orders <= 6 keep all P outputs of a target in one thread; above, the
+// outputs are split between NS threads (registers).
+__host__ __device__ constexpr int dir_splits(int D, int rho) { return D == 2 ? 1 : (rho <= 6 ? 1 : rho == 7 ? 2 : 4); }
+
+template <int D, int NS>
+struct DirTile {
+    static constexpr int T = kDirThreads / NS;                                   // targets per CTA
+    static constexpr int X = D == 2 ? 16 : (NS == 4 ? 4 : 8);
+    static constexpr int Y = D == 2 ? T / 16 : (NS == 1 ? 8 : 4);
+    static constexpr int Z = D == 2 ? 1 : T / (X * Y);
+    static constexpr int RX = X + 2, RY = Y + 2, RZ = D == 2 ? 1 : Z + 2;        // staged source rows
+    static constexpr int NR = RX * RY * RZ;
+    static constexpr int NV = D == 2 ? 9 : 27;                                   // offsets per source class
+};
+
+// shared-memory row pitch (floats): Pp, or Pp + 4 when Pp / 4 is even
+__host__ __device__ constexpr int dir_pitch(int Pp) { return ((Pp / 4) & 1) ? Pp : Pp + 4; }
+
+template <int D, int RHO>
+__host__ __device__ constexpr size_t dir_smem() {
+    constexpr int NS = dir_splits(D, RHO), Pp = pad4(ncoef(D, RHO));
+    using Tl = DirTile<D, NS>;
+    return (size_t)Tl::NR * dir_pitch(Pp) * 4 + (size_t)Tl::NV * Pp * 4 + 16;
 }
 
-cudaError_t launch_m2l_simple(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
+// Cost of output k (the inputs b it takes) and the balanced split of the graded outputs into NS
+// contiguous ranges: split s covers [dir_k0(s), dir_k0(s + 1)).
+__host__ __device__ constexpr int dir_k0(int D, int rho, int NS, int s) {
+    if (s <= 0) return 0;
+    const int P = ncoef(D, rho);
+    if (s >= NS) return P;
+    long total = 0;
+    for (int d = 0; d <= rho; ++d) total += (long)ncoef(D, d) * ncoef(D, rho - d) - (d ? (long)ncoef(D, d - 1) * ncoef(D, rho - d) : 0);
+    // total = sum over k of ncoef(D, rho - |k|); cut where the running cost passes s / NS of it
+    long run = 0;
+    int k = 0;
+    for (int d = 0; d <= rho; ++d) {
+        const int cnt = ncoef(D, d) - (d ? ncoef(D, d - 1) : 0);
+        for (int j = 0; j < cnt; ++j, ++k) {
+            if (run * NS >= total * s) return k;
+            run += ncoef(D, rho - d);
+        }
+    }
+    return P;
+}
+
+// The (k, b) pairs of the outputs [K0, K1): every k in the range with every b, |k| + |b| <= RHO,
+// ordered by b; entry = (k, b, index of k + b), all graded indices.  Built at compile time.
+template <int D, int RHO, int K0, int K1>
+struct DirPairs {
+    static constexpr int count() {
+        int c = 0;
+        for (int bd = 0; bd <= RHO; ++bd)
+            for (int b0 = bd; b0 >= 0; --b0)
+                for (int b1 = bd - b0; b1 >= 0; --b1) {
+                    if (D == 2 && bd - b0 - b1 != 0) continue;
+                    for (int kd = 0; kd + bd <= RHO; ++kd)
+                        for (int k0 = kd; k0 >= 0; --k0)
+                            for (int k1 = kd - k0; k1 >= 0; --k1) {
+                                if (D == 2 && kd - k0 - k1 != 0) continue;
+                                const int ki = gidx<D>(k0, k1, kd - k0 - k1);
+                                if (ki >= K0 && ki < K1) ++c;
+                            }
+                }
+        return c;
+    }
+    static constexpr int N = count();
+    short k[N > 0 ? N : 1], b[N > 0 ? N : 1], m[N > 0 ? N : 1];
+    constexpr DirPairs() : k{}, b{}, m{} {
+        int c = 0;
+        for (int bd = 0; bd <= RHO; ++bd)
+            for (int b0 = bd; b0 >= 0; --b0)
+                for (int b1 = bd - b0; b1 >= 0; --b1) {
+                    const int b2 = bd - b0 - b1;
+                    if (D == 2 && b2 != 0) continue;
+                    for (int kd = 0; kd + bd <= RHO; ++kd)
+                        for (int k0 = kd; k0 >= 0; --k0)
+                            for (int k1 = kd - k0; k1 >= 0; --k1) {
+                                const int k2 = kd - k0 - k1;
+                                if (D == 2 && k2 != 0) continue;
+                                const int ki = gidx<D>(k0, k1, k2);
+                                if (ki < K0 || ki >= K1) continue;
+                                k[c] = (short)ki;
+                                b[c] = (short)gidx<D>(b0, b1, b2);
+                                m[c] = (short)gidx<D>(k0 + b0, k1 + b1, k2 + b2);
+                                ++c;
+                            }
+                }
+    }
+};
+
+// one pair: acc[k - K0] += Dt(m) Mt(b); the moment value comes from the 16-byte group of b and
+// the derivative value from the offset's row (repeated reads of one address are merged)
+template <int K0, int KB, int BB, int MB, int NACC>
+__device__ __forceinline__ void dir_fma(const float *__restrict__ row, const float *__restrict__ drow,
+                                        float (&acc)[NACC]) {
+    const float4 mv4 = *reinterpret_cast<const float4 *>(row + (BB & ~3));
+    const float mv = (BB & 3) == 0 ? mv4.x : (BB & 3) == 1 ? mv4.y : (BB & 3) == 2 ? mv4.z : mv4.w;
+    const float4 dv4 = *reinterpret_cast<const float4 *>(drow + (MB & ~3));
+    const float dv = (MB & 3) == 0 ? dv4.x : (MB & 3) == 1 ? dv4.y : (MB & 3) == 2 ? dv4.z : dv4.w;
+    acc[KB - K0] = fmaf(dv, mv, acc[KB - K0]);
+}
+
+template <int D, int RHO, int K0, int K1, int NACC, size_t... I>
+__device__ __forceinline__ void dir_body_seq(const float *__restrict__ row, const float *__restrict__ drow,
+                                             float (&acc)[NACC], std::index_sequence<I...>) {
+    constexpr DirPairs<D, RHO, K0, K1> T{};
+    (dir_fma<K0, T.k[I], T.b[I], T.m[I], NACC>(row, drow, acc), ...);
+}
+
+// Outputs [K0, K1) of one target for one offset: acc[k - K0] += Dt(k + b) Mt(b) over
+// |k| + |b| <= RHO.  `row` is the source's staged moment row, `drow` the offset's derivative row.
+template <int D, int RHO, int K0, int K1, int NACC>
+__device__ __forceinline__ void dir_body(const float *__restrict__ row, const float *__restrict__ drow,
+                                         float (&acc)[NACC]) {
+    dir_body_seq<D, RHO, K0, K1, NACC>(row, drow, acc, std::make_index_sequence<DirPairs<D, RHO, K0, K1>::N>{});
+}
+
+template <int D, int RHO, int NS, int S>
+struct DirSplit {
+    static constexpr int K0 = dir_k0(D, RHO, NS, S), K1 = dir_k0(D, RHO, NS, S + 1);
+    static constexpr int N = K1 - K0 > 0 ? K1 - K0 : 1;
+};
+
+// One split's whole work for one target: every source class, every offset of its window.
+template <int D, int RHO, int NS, int S>
+__device__ __forceinline__ void dir_accumulate(const float *rows, const float *drow, int ix, int iy, int iz, int cls,
+                                               int sp, bool finest, float (&acc)[DirSplit<D, RHO, NS, S>::N]) {
+    using Tl = DirTile<D, NS>;
+    constexpr int Pp = pad4(ncoef(D, RHO)), PITCH = dir_pitch(Pp);
+#pragma unroll 1
+    for (int j = 0; j < Tl::NV; ++j) {
+        const int dx = j % 3 - 1, dy = (j / 3) % 3 - 1, dz = D == 3 ? j / 9 - 1 : 0;
+        const int ox = 2 * dx + (sp & 1) - (cls & 1);
+        const int oy = 2 * dy + ((sp >> 1) & 1) - ((cls >> 1) & 1);
+        const int oz = D == 3 ? 2 * dz + ((sp >> 2) & 1) - ((cls >> 2) & 1) : 0;
+        // the hole: interactions of near cells are resolved at the finer level
+        if (!finest && ox >= -1 && ox <= 1 && oy >= -1 && oy <= 1 && oz >= -1 && oz <= 1) continue;
+        const int r = (ix + dx + 1) + Tl::RX * ((iy + dy + 1) + Tl::RY * (D == 3 ? iz + dz + 1 : 0));
+        dir_body<D, RHO, DirSplit<D, RHO, NS, S>::K0, DirSplit<D, RHO, NS, S>::K1, DirSplit<D, RHO, NS, S>::N>(
+            rows + r * PITCH, drow + j * Pp, acc);
+    }
+}
+
+template <int D, int RHO, int NS, int S>
+__device__ __forceinline__ void dir_store(float *L, int64_t tlin, const float (&acc)[DirSplit<D, RHO, NS, S>::N]) {
+    constexpr int P = ncoef(D, RHO), Pp = pad4(P);
+    constexpr int K0 = DirSplit<D, RHO, NS, S>::K0, K1 = DirSplit<D, RHO, NS, S>::K1;
+    float *dst = L + tlin * Pp;
+#pragma unroll
+    for (int kd = 0; kd <= RHO; ++kd)
+#pragma unroll
+        for (int k0 = kd; k0 >= 0; --k0)
+#pragma unroll
+            for (int k1 = kd - k0; k1 >= 0; --k1) {
+                const int k2 = kd - k0 - k1;
+                if (D == 2 && k2 != 0) continue;
+                const int ki = gidx<D>(k0, k1, k2);
+                if (ki < K0 || ki >= K1) continue;
+                dst[ki] = (kd & 1) ? -acc[ki - K0] : acc[ki - K0];
+            }
+    if (K1 == P)
+#pragma unroll
+        for (int k = P; k < Pp; ++k) dst[k] = 0.0f;   // row padding stays zero
+}
+
+template <int D, int RHO, int NS, int S>
+__device__ __forceinline__ void dir_run(const float *rows, const float *drow, uint64_t *bar, const float *M,
+                                        float *L, const float *dtab, int n, int finest, int *err, int cls,
+                                        int ox0, int oy0, int oz0, int ix, int iy, int iz, bool valid) {
+    using Tl = DirTile<D, NS>;
+    constexpr int Pp = pad4(ncoef(D, RHO)), PITCH = dir_pitch(Pp);
+    const int half = n >> 1;
+    float acc[DirSplit<D, RHO, NS, S>::N];
+#pragma unroll
+    for (int k = 0; k < DirSplit<D, RHO, NS, S>::N; ++k) acc[k] = 0.0f;
+    // rows of the staged box that lie in the grid (the same for every source class)
+    auto in_count = [&](int o0, int R) { return max(0, min(half, o0 - 1 + R) - max(0, o0 - 1)); };
+    const uint32_t nin = (uint32_t)in_count(ox0, Tl::RX) * (uint32_t)in_count(oy0, Tl::RY) *
+                         (uint32_t)(D == 3 ? in_count(oz0, Tl::RZ) : 1);
+    const uint32_t bytes = (nin + Tl::NV) * (uint32_t)Pp * 4u;
+#pragma unroll 1
+    for (int sp = 0; sp < (1 << D); ++sp) {
+        __syncthreads();                        // the previous class's rows are no longer read
+        tc::fence_proxy_async_smem();           // (before the copies overwrite them)
+        if (threadIdx.x == 0) tc::mbar_arrive_expect_tx(bar, bytes);
+        __syncthreads();
+        float *rws = const_cast<float *>(rows);
+        for (int r = threadIdx.x; r < Tl::NR; r += kDirThreads) {
+            const int rx = r % Tl::RX, ry = (r / Tl::RX) % Tl::RY, rz = r / (Tl::RX * Tl::RY);
+            const int ax = ox0 + rx - 1, ay = oy0 + ry - 1, az = D == 3 ? oz0 + rz - 1 : 0;
+            if (ax >= 0 && ax < half && ay >= 0 && ay < half && az >= 0 && (D == 2 || az < half)) {
+                const int64_t cell = (2 * ax + (sp & 1)) +
+                                     (int64_t)n * ((2 * ay + ((sp >> 1) & 1)) + (int64_t)n * (D == 3 ? 2 * az + ((sp >> 2) & 1) : 0));
+                tc::bulk_g2s(rws + r * PITCH, M + cell * Pp, Pp * 4u, bar);
+            } else {
+                float4 *z = reinterpret_cast<float4 *>(rws + r * PITCH);
+#pragma unroll
+                for (int c = 0; c < Pp / 4; ++c) z[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        for (int j = threadIdx.x; j < Tl::NV; j += kDirThreads) {
+            const int dx = j % 3 - 1, dy = (j / 3) % 3 - 1, dz = D == 3 ? j / 9 - 1 : 0;
+            const int ox = 2 * dx + (sp & 1) - (cls & 1);
+            const int oy = 2 * dy + ((sp >> 1) & 1) - ((cls >> 1) & 1);
+            const int oz = D == 3 ? 2 * dz + ((sp >> 2) & 1) - ((cls >> 2) & 1) : 0;
+            const int olin = (ox + 3) + 7 * (oy + 3) + (D == 3 ? 49 * (oz + 3) : 0);
+            tc::bulk_g2s(const_cast<float *>(drow) + j * Pp, dtab + (int64_t)olin * Pp, Pp * 4u, bar);
+        }
+        const bool ok = tc::mbar_wait(bar, (uint32_t)(sp & 1), err, 2048);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not land within the bounded wait: let the copies in flight finish (again
+            // bounded) before the CTA's shared memory is released, and leave the outputs alone
+            tc::mbar_wait(bar, (uint32_t)(sp & 1), err, 2048);
+            return;
+        }
+        if (valid) dir_accumulate<D, RHO, NS, S>(rows, drow, ix, iy, iz, cls, sp, finest != 0, acc);
+    }
+    if (valid) {
+        const int tx = 2 * (ox0 + ix) + (cls & 1), ty = 2 * (oy0 + iy) + ((cls >> 1) & 1);
+        const int tz = D == 3 ? 2 * (oz0 + iz) + ((cls >> 2) & 1) : 0;
+        dir_store<D, RHO, NS, S>(L, tx + (int64_t)n * (ty + (int64_t)n * tz), acc);
+    }
+}
+
+template <int D, int RHO>
+__global__ void __launch_bounds__(kDirThreads, 1) k_m2l_dir(const float *__restrict__ M, float *__restrict__ L,
+                                                            const float *__restrict__ dtab, int n, int finest,
+                                                            int *__restrict__ err) {
+    constexpr int NS = dir_splits(D, RHO), Pp = pad4(ncoef(D, RHO));
+    using Tl = DirTile<D, NS>;
+    extern __shared__ __align__(16) float sm[];
+    float *rows = sm;
+    float *drow = rows + Tl::NR * dir_pitch(Pp);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(drow + Tl::NV * Pp);
+    const int half = n >> 1;
+    const int tx = (half + Tl::X - 1) / Tl::X, ty = (half + Tl::Y - 1) / Tl::Y;
+    const int tz = D == 3 ? (half + Tl::Z - 1) / Tl::Z : 1;
+    const int ntile = tx * ty * tz;
+    const int cls = (int)blockIdx.x / ntile, tile = (int)blockIdx.x % ntile;
+    const int ox0 = (tile % tx) * Tl::X, oy0 = ((tile / tx) % ty) * Tl::Y, oz0 = (tile / (tx * ty)) * Tl::Z;
+    const int warp = (int)threadIdx.x >> 5, lane = (int)threadIdx.x & 31;
+    const int split = warp % NS;                               // warp-uniform
+    const int i = (warp / NS) * 32 + lane;                     // target within the tile
+    const int ix = i % Tl::X, iy = (i / Tl::X) % Tl::Y, iz = i / (Tl::X * Tl::Y);
+    const bool valid = ox0 + ix < half && oy0 + iy < half && (D == 2 || oz0 + iz < half);
+    if (threadIdx.x == 0) tc::mbar_init(bar, 1);
+    __syncthreads();
+    // every warp runs the same barriers; the split only selects the compile-time output range
+    if (NS == 1 || split == 0)
+        dir_run<D, RHO, NS, 0>(rows, drow, bar, M, L, dtab, n, finest, err, cls, ox0, oy0, oz0, ix, iy, iz, valid);
+    else if (NS >= 2 && split == 1)
+        dir_run<D, RHO, NS, (NS >= 2 ? 1 : 0)>(rows, drow, bar, M, L, dtab, n, finest, err, cls, ox0, oy0, oz0, ix, iy, iz, valid);
+    else if (NS >= 4 && split == 2)
+        dir_run<D, RHO, NS, (NS >= 4 ? 2 : 0)>(rows, drow, bar, M, L, dtab, n, finest, err, cls, ox0, oy0, oz0, ix, iy, iz, valid);
+    else if (NS >= 4)
+        dir_run<D, RHO, NS, (NS >= 4 ? 3 : 0)>(rows, drow, bar, M, L, dtab, n, finest, err, cls, ox0, oy0, oz0, ix, iy, iz, valid);
+}
+
+template <int D, int RHO>
+cudaError_t dir_launch(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
+    constexpr int NS = dir_splits(D, RHO);
+    using Tl = DirTile<D, NS>;
+    constexpr size_t smem = dir_smem<D, RHO>();
+    static_assert(smem <= 227 * 1024, "the staged rows exceed a CTA's shared memory");
     const Level &lv = pl->lev[level];
     const int half = lv.n >> 1;
-    int64_t Gh = 1;
-    for (int d = 0; d < pl->D; ++d) Gh *= half;
-    const int64_t nbp = (Gh + kM2LThreads - 1) / kM2LThreads;
-    const float *M = pl->d_M + lv.off * pl->Pp;
-    float *L = pl->d_L + lv.off * pl->Pp;
-    const int nofs = pl->D == 3 ? 343 : 49;
-    const float *dt = pl->d_dtab + (int64_t)level * nofs * pl->Pp;
-    dim3 grid((unsigned)(nbp << pl->D), (unsigned)pl->P);
-    pl->launches[FC2T2_STAGE_M2L] += 1;
-    k_m2l_simple<<<grid, kM2LThreads, 0, s>>>(M, L, lv.n, pl->D, pl->Pp, level == 0 ? 1 : 0, dt,
-                                              pl->d_m2l_start, pl->d_m2l_pairs);
+    const int ntile = ((half + Tl::X - 1) / Tl::X) * ((half + Tl::Y - 1) / Tl::Y) *
+                      (D == 3 ? (half + Tl::Z - 1) / Tl::Z : 1);
+    const int nofs = D == 3 ? 343 : 49;
+    auto *fn = k_m2l_dir<D, RHO>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    fn<<<(unsigned)(ntile << D), kDirThreads, smem, s>>>(pl->d_M + lv.off * pl->Pp, pl->d_L + lv.off * pl->Pp,
+                                                          pl->d_dtab + (int64_t)level * nofs * pl->Pp, lv.n,
+                                                          level == 0 ? 1 : 0, pl->d_flags + 2);
     return cudaGetLastError();
 }
 
+}  // namespace
+
 cudaError_t launch_m2l(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
-    return launch_m2l_simple(pl, s, level);
+    pl->launches[FC2T2_STAGE_M2L] += 1;
+    FC2T2_DISPATCH(pl->D, pl->rho, return (dir_launch<D_, R_>(pl, s, level)), return cudaErrorInvalidValue);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace fc2t2
