@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the oracle error check")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the ray-query (33.5M queries) and large fitting (2^24 points) workloads")
     return ap.parse_args()
 
 
@@ -566,6 +568,128 @@ def measure_rays(dev, flush, steps, warmup):
     return out
 
 
+def measure_ray_queries(args, world, dev, flush, modes=("separable", "bf16x3", "tf32", "bf16"), n_ref=8192):
+    """The ray-query workload as point queries: 2^18 sphere-surface sources, 512 x 512 pinhole rays x
+    128 stratified samples (33,554,432 queries), 64^3, order 8, sigma 0.01; a forward + backward
+    step per M2L form (the separable FP32 passes, BF16 x 3, and the mixed TF32 and BF16 forms), each
+    with its error against the FP64 oracle at `n_ref` seeded queries (y) and sources (wbar, pbar)."""
+    from paper_2111_00110_gb300 import workloads
+    wl = workloads.sphere_rays()
+    ref = None if args.no_check else oracle_reference_sample(wl, n=n_ref)
+    out = {"workload": "sphere_rays: 2^18 sphere-surface sources, 512 x 512 rays x 128 samples",
+           "N": wl.N, "M": wl.M, "grid": wl.grid, "order": wl.order, "sigma": wl.sigma,
+           "unit": UNIT, "error_sample": f"{n_ref} seeded queries (y) and {n_ref} seeded sources (wbar, pbar)",
+           "forms": {}}
+    peaks = load_peaks()
+    for mode in modes:
+        m = measure_mode(mode, wl, args, world, dev, flush, ref=ref, steps=min(args.steps, 5))
+        out["forms"][mode] = {"value": m.value, "ms_per_step": m.ms_per_step, "rel_l2_vs_oracle": m.err,
+                              "stage_ms_per_step": m.stage_ms, "roofline": roofline_for(m, peaks)}
+    return out
+
+
+def measure_fit(dev, flush, steps, n=1 << 24, adam_steps=100, n_ref=2048, check=True):
+    """The large fitting loop: 2^24 sources from 64 anisotropic Gaussians, 2^24 uniform queries,
+    128^3, order 8, sigma 0.005, mixed-precision (TF32) M2L; targets from the ground-truth set, w
+    initialised to 0.1 N(0,1) (seed 5002), Adam (lr 1e-3) on (w, p) through the autograd layer.
+    Reports one timed forward + backward step, the device memory it holds (the library's plan
+    workspace and the step's tensors; the backward rebuilds its own expansion from (q, ybar), so no
+    expansion of the forward is kept), step 0 against the oracle at `n_ref` samples, and the loss
+    over `adam_steps` steps."""
+    import numpy as np
+    import torch
+    from paper_2111_00110_gb300 import workloads
+    from paper_2111_00110_gb300.transform import Plan, fc2t2
+    gt = workloads.fit_large(N=n, M=n)
+    torch.cuda.synchronize(dev)
+    free0, total = torch.cuda.mem_get_info(dev)
+    plan = Plan(3, gt.grid, gt.order, gt.sigma, m2l="tf32", max_sources=n, max_queries=n, device=dev)
+    torch.cuda.synchronize(dev)
+    free1, _ = torch.cuda.mem_get_info(dev)
+    q = torch.from_numpy(gt.q).to(dev)
+    with torch.no_grad():
+        target = plan.forward(torch.from_numpy(gt.p).to(dev), torch.from_numpy(gt.w).to(dev), q)
+    w0 = (0.1 * np.random.default_rng(5002).standard_normal(n)).astype(np.float32)
+    p = torch.from_numpy(gt.p).to(dev).requires_grad_(True)
+    w = torch.from_numpy(w0).to(dev).requires_grad_(True)
+    stream = torch.cuda.current_stream(dev)
+
+    def loss_and_grad():
+        y = fc2t2(p, w, q, plan)
+        loss = torch.mean((y - target) ** 2)
+        loss.backward()
+        return y, loss
+
+    # step 0: the oracle check on samples, and the timed forward + backward
+    y, loss0 = loss_and_grad()
+    torch.cuda.synchronize(dev)
+    err = None
+    if check:
+        import oracle
+        d = oracle.OracleDesc(dim=3, grid=gt.grid, order=gt.order, sigma=gt.sigma)
+        rng = np.random.default_rng(7)
+        sq = np.sort(rng.choice(n, size=n_ref, replace=False))
+        sp = np.sort(rng.choice(n, size=n_ref, replace=False))
+        f64 = lambda a: np.asarray(a, dtype=np.float64)
+        yo = oracle.forward(d, f64(gt.p), f64(w0), f64(gt.q), sel=sq)
+        ybar = (2.0 / n) * (y - target).detach().cpu().numpy()
+        wo, po = oracle.backward(d, f64(gt.p), f64(w0), f64(gt.q), f64(ybar), sel=sp)
+        err = {"y": rel_l2(y.detach().cpu().numpy()[sq], yo), "wbar": rel_l2(w.grad.cpu().numpy()[sp], wo),
+               "pbar": rel_l2(p.grad.cpu().numpy()[sp], po)}
+    torch.cuda.reset_peak_memory_stats(dev)
+    for _ in range(2):
+        w.grad = None
+        p.grad = None
+        loss_and_grad()
+    torch.cuda.synchronize(dev)
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        w.grad = None
+        p.grad = None
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        loss_and_grad()
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        total_ms += a.elapsed_time(b)
+    ms = total_ms / steps
+    free2, _ = torch.cuda.mem_get_info(dev)
+    mem = {"plan_workspace_bytes": int(free0 - free1), "device_in_use_after_steps_bytes": int(free0 - free2),
+           "torch_peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+           "finest_expansion_bytes": int(gt.grid ** 3 * plan.info()["coefficients"] * 4)}
+    # the loop
+    with torch.no_grad():
+        w.copy_(torch.from_numpy(w0).to(dev))
+        p.copy_(torch.from_numpy(gt.p).to(dev))
+    opt = torch.optim.Adam([w, p], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    hi = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
+    losses = []
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    loss_t = []
+    for _ in range(adam_steps):
+        opt.zero_grad()
+        with torch.no_grad():
+            p.clamp_(0.0, hi)
+        _, loss = loss_and_grad()
+        opt.step()
+        loss_t.append(loss.detach())
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    losses = [float(x) for x in loss_t]
+    plan.check()
+    plan.close()
+    return {"workload": "fit_large: 2^24 sources (64 anisotropic Gaussians), 2^24 uniform queries",
+            "N": n, "M": n, "grid": gt.grid, "order": gt.order, "sigma": gt.sigma, "m2l": "tf32",
+            "value": n / (ms / 1e3), "unit": "query-evals/s (fwd+bwd through the autograd layer)",
+            "ms_per_step": ms, "steps": steps, "step0_rel_l2_vs_oracle": err,
+            "memory": mem,
+            "adam": {"steps": adam_steps, "lr": 1e-3, "ms_total": a.elapsed_time(b),
+                     "loss": {str(i): losses[i] for i in range(0, adam_steps, 10)} | {str(adam_steps - 1): losses[-1]}}}
+
+
 def measure_batched(dev, flush, steps, warmup, n_inst=64):
     """The batched workload: 64 independent clustered point sets (N_i = M_i log-uniform in
     [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3) and order (4 or 6) chosen by the
@@ -657,6 +781,9 @@ def run_ours(args, rank, world, local_rank):
                                               steps=min(args.steps, 10), fit=True)
     rays = measure_rays(dev, flush, min(args.steps, 10), args.warmup) if (args.m2l == "auto" and rank == 0) else None
     batched = measure_batched(dev, flush, min(args.steps, 5), args.warmup) if (args.m2l == "auto" and rank == 0) else None
+    extra = args.m2l == "auto" and rank == 0 and not args.no_extra
+    ray_queries = measure_ray_queries(args, world, dev, flush) if extra else None
+    fit = measure_fit(dev, flush, min(args.steps, 5), check=not args.no_check) if extra else None
     if rank != 0:
         return
     peaks = load_peaks()
@@ -697,6 +824,8 @@ def run_ours(args, rank, world, local_rank):
         "stage_ms_per_step": main.stage_ms,
         "variants": {k: summary(v) for k, v in variants.items()},
         "ray_integrals": rays,
+        "ray_queries": ray_queries,
+        "fit_large": fit,
         "batched": batched,
         "cpu_baseline": cpu,
     }

@@ -269,7 +269,7 @@ static void destroy(fc2t2_plan_s *pl) {
     if (pl->ev_run_fork) cudaEventDestroy(pl->ev_run_fork);
     if (pl->ev_run_done) cudaEventDestroy(pl->ev_run_done);
     cudaFree(pl->d_M); cudaFree(pl->d_L); cudaFree(pl->d_hold); cudaFree(pl->d_dtab);
-    cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags);
+    cudaFree(pl->d_scan_tmp); cudaFree(pl->d_flags); cudaFree(pl->d_over); cudaFree(pl->d_over_ctr);
     cudaFree(pl->d_mma_ops);
     for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
     cudaFree(pl->sep.d_t);
@@ -588,6 +588,12 @@ fc2t2_status fc2t2_plan_create(const fc2t2_plan_desc *desc, fc2t2_plan *out) {
     while (tiles > 1) { tmp += 2 * tiles + 1; tiles = (tiles + 4095) / 4096; }
     pl->scan_tmp_len = tmp;
     if ((st = dev_alloc(&pl->d_scan_tmp, 2 * (size_t)tmp, "scan workspace")) != FC2T2_OK) { destroy(pl); return st; }
+    if ((st = dev_alloc(&pl->d_over, (size_t)G0, "P2M overflow list")) != FC2T2_OK ||
+        (st = dev_alloc(&pl->d_over_ctr, 2, "P2M overflow counters")) != FC2T2_OK ||
+        (st = check_cuda(cudaMemset(pl->d_over_ctr, 0, 2 * sizeof(unsigned long long)), "clear counters")) != FC2T2_OK) {
+        destroy(pl);
+        return st;
+    }
     if ((st = alloc_sort(pl->src, desc->max_sources, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
     if ((st = alloc_sort(pl->qry, desc->max_queries, G0, pl->D)) != FC2T2_OK) { destroy(pl); return st; }
     pl->src.scan_tmp = pl->d_scan_tmp;

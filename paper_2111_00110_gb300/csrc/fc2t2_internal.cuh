@@ -163,6 +163,8 @@ struct fc2t2_plan_s {
     int *d_scan_tmp = nullptr;    // block sums of the prefix scan
     int64_t scan_tmp_len = 0;
     int *d_flags = nullptr;       // [4] device error flags
+    int2 *d_over = nullptr;       // [G0] P2M's overflow list: (cell, first chunk) of cells past the cap
+    unsigned long long *d_over_ctr = nullptr;   // [2] the list's (entries << 32 | chunks), blocks done
     fc2t2::SortWork src, qry;
     void *d_mma_ops = nullptr;    // tensor-core M2L operator images (TF32 / BF16 modes)
     size_t mma_ops_bytes = 0;

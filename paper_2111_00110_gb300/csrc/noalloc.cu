@@ -46,6 +46,7 @@ constexpr size_t kScratchBytes =
     2 * align256(sizeof(float) * kNaMaxCellsAllLevels * kNaMaxPp) +                  // M, L
     align256(sizeof(float) * kNaMaxLevels * kNaOffsets * kNaMaxPp) +                 // dtab
     align256(sizeof(int) * 64) + align256(sizeof(int) * 4) +                         // scan, flags
+    align256(sizeof(int2) * kNaMaxCells) + align256(sizeof(unsigned long long) * 2) + // P2M overflow list
     2 * kSortBytes;
 
 }  // namespace
@@ -186,6 +187,8 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     pl.d_dtab = carve<float>(base, off, (size_t)kNaMaxLevels * kNaOffsets * kNaMaxPp);
     pl.d_scan_tmp = carve<int>(base, off, 64);
     pl.d_flags = carve<int>(base, off, 4);
+    pl.d_over = carve<int2>(base, off, kNaMaxCells);
+    pl.d_over_ctr = carve<unsigned long long>(base, off, 2);
     SortWork *sorts[2] = {&pl.src, &pl.qry};
     for (SortWork *sw : sorts) {
         sw->cap = kNaMaxPoints;
@@ -203,6 +206,8 @@ extern "C" FC2T2_API fc2t2_status fc2t2_forward_noalloc(const fc2t2_plan_desc *d
     k_na_tables<<<pl.nlev * nofs, 64, 0, s>>>(pl.d_dtab, pl.D, pl.rho, pl.Pp, nofs, desc->sigma, pl.lev[0].h);
     if ((st = check_cuda(cudaGetLastError(), "operator tables")) != FC2T2_OK) return st;
     if ((st = check_cuda(cudaMemsetAsync(pl.d_flags, 0, 4 * sizeof(int), s), "clear flags")) != FC2T2_OK) return st;
+    if ((st = check_cuda(cudaMemsetAsync(pl.d_over_ctr, 0, 2 * sizeof(unsigned long long), s), "clear counters")) != FC2T2_OK)
+        return st;
     if (N == 0) return check_cuda(cudaMemsetAsync(y, 0, sizeof(float) * M, s), "zero y");
 
     // the same kernels as fc2t2_forward, on scratch-array pointers

@@ -22,12 +22,56 @@
 namespace fc2t2 {
 
 constexpr int kP2MThreads = 64;
+// A P2M thread takes at most kP2MCap points of its cell; the points of a cell beyond its first
+// kP2MCap (clustered sources, or the many samples of rays that cross a cell) are summed by a second
+// kernel, in chunks of kP2MCap consecutive sorted points spread over the whole GPU, and added to
+// the cell's row with float atomics.  So no thread waits on a cell much fuller than the mean.
+constexpr int kP2MCap = 32;
+
+// acc += w u^b / b! for one point (u = (x - z) / h per dimension)
+template <int D, int RHO>
+__device__ __forceinline__ void p2m_add(float (&acc)[ncoef(D, RHO)], const float4 r, const float (&z)[3], float inv_h) {
+    const float xj[3] = {r.x, r.y, r.z};
+    float pw[3][RHO + 1];
+#pragma unroll
+    for (int d = 0; d < D; ++d) power_ladder<RHO>((xj[d] - z[d]) * inv_h, pw[d]);
+    const float wj = r.w;
+#pragma unroll
+    for (int a0 = 0; a0 <= RHO; ++a0) {
+        const float t0 = wj * pw[0][a0];
+#pragma unroll
+        for (int a1 = 0; a1 <= RHO; ++a1) {
+            if (a0 + a1 > RHO) continue;
+            if (D == 2) {
+                acc[gidx2(a0, a1)] = fmaf(t0, pw[1][a1], acc[gidx2(a0, a1)]);
+            } else {
+                const float t01 = t0 * pw[1][a1];
+#pragma unroll
+                for (int a2 = 0; a2 <= RHO; ++a2) {
+                    if (a0 + a1 + a2 > RHO) continue;
+                    acc[gidx3(a0, a1, a2)] = fmaf(t01, pw[2][a2], acc[gidx3(a0, a1, a2)]);
+                }
+            }
+        }
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void cell_centre(int64_t c, int n, float lo, float h, float (&z)[3]) {
+    z[0] = z[1] = z[2] = 0.0f;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        z[d] = lo + ((float)(int)(c % n) + 0.5f) * h;
+        c /= n;
+    }
+}
 
 template <int D, int RHO>
 __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ rec,
                                                      const int *__restrict__ start, int n,
                                                      int64_t G, float lo, float h, float inv_h,
-                                                     float *__restrict__ M, int *__restrict__ err) {
+                                                     float *__restrict__ M, int *__restrict__ err,
+                                                     int2 *__restrict__ over, unsigned long long *over_ctr) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     extern __shared__ float4 smem4[];   // the block's sorted records, then its output rows
     __shared__ uint64_t staged;
@@ -53,40 +97,13 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
 #pragma unroll
     for (int k = 0; k < P; ++k) acc[k] = 0.0f;
     if (c < G) {
-        int cc[3] = {0, 0, 0};
-        int64_t r = c;
-#pragma unroll
-        for (int d = 0; d < D; ++d) { cc[d] = (int)(r % n); r /= n; }
         float z[3];
-#pragma unroll
-        for (int d = 0; d < D; ++d) z[d] = lo + ((float)cc[d] + 0.5f) * h;
-        const int j0 = start[c], j1 = start[c + 1];
+        cell_centre<D>(c, n, lo, h, z);
+        const int j0 = start[c], j1 = min(start[c + 1], j0 + kP2MCap);
         const bool have = nst > 0 && j1 > j0 && tc::mbar_wait(&staged, 0, err, 1024);
         for (int j = j0; j < j1; ++j) {
             const float4 r = (have && j - jb0 < nst) ? smem4[j - jb0] : __ldg(rec + j);
-            const float xj[3] = {r.x, r.y, r.z};
-            float pw[3][RHO + 1];
-#pragma unroll
-            for (int d = 0; d < D; ++d) power_ladder<RHO>((xj[d] - z[d]) * inv_h, pw[d]);
-            const float wj = r.w;
-#pragma unroll
-            for (int a0 = 0; a0 <= RHO; ++a0) {
-                const float t0 = wj * pw[0][a0];
-#pragma unroll
-                for (int a1 = 0; a1 <= RHO; ++a1) {
-                    if (a0 + a1 > RHO) continue;
-                    if (D == 2) {
-                        acc[gidx2(a0, a1)] = fmaf(t0, pw[1][a1], acc[gidx2(a0, a1)]);
-                    } else {
-                        const float t01 = t0 * pw[1][a1];
-#pragma unroll
-                        for (int a2 = 0; a2 <= RHO; ++a2) {
-                            if (a0 + a1 + a2 > RHO) continue;
-                            acc[gidx3(a0, a1, a2)] = fmaf(t01, pw[2][a2], acc[gidx3(a0, a1, a2)]);
-                        }
-                    }
-                }
-            }
+            p2m_add<D, RHO>(acc, r, z, inv_h);
         }
     }
     __syncthreads();   // every staged record has been read before the buffer takes the output rows
@@ -97,6 +114,82 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
     const int total4 = (int)(ncell * Pp / 4);
     float4 *dst = reinterpret_cast<float4 *>(M + c0 * Pp);
     for (int i = threadIdx.x; i < total4; i += kP2MThreads) dst[i] = smem4[i];
+
+    // The cells of the block with points beyond their first kP2MCap append themselves to the
+    // plan's overflow list: one 64-bit atomic per block reserves (entries, chunks) -- entry =
+    // (cell, index of its first chunk of kP2MCap points in the list's chunk numbering) -- so the
+    // entries come out ordered by chunk index.  k_p2m_over sums the chunks.
+    const int cnt = c < G ? start[c + 1] - start[c] : 0;
+    const int nch = cnt > kP2MCap ? (cnt - 1) / kP2MCap : 0;        // chunks past the first kP2MCap
+    if (!__syncthreads_or(nch > 0)) return;
+    __shared__ int s_warp[kP2MThreads / 32][2];
+    __shared__ unsigned long long s_base;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = nch;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const unsigned heavy = __ballot_sync(0xffffffffu, nch > 0);
+    if (lane == 31) { s_warp[warp][0] = incl; s_warp[warp][1] = __popc(heavy); }
+    __syncthreads();
+    int chunk_before = 0, entry_before = 0, chunks = 0, entries = 0;
+#pragma unroll
+    for (int v = 0; v < kP2MThreads / 32; ++v) {
+        if (v < warp) { chunk_before += s_warp[v][0]; entry_before += s_warp[v][1]; }
+        chunks += s_warp[v][0];
+        entries += s_warp[v][1];
+    }
+    if (threadIdx.x == 0)
+        s_base = atomicAdd(over_ctr, ((unsigned long long)entries << 32) | (unsigned long long)chunks);
+    __syncthreads();
+    if (nch > 0) {
+        const int e = (int)(s_base >> 32) + entry_before + __popc(heavy & ((1u << lane) - 1u));
+        over[e] = make_int2((int)c, (int)(s_base & 0xffffffffu) + chunk_before + incl - nch);
+    }
+}
+
+// The overflow chunks of one P2M: a grid-stride loop over the list's chunks; chunk i belongs to the
+// last entry whose first chunk is <= i (binary search), and covers kP2MCap consecutive sorted
+// points of that cell past its first kP2MCap.  Each chunk's sum is added to the cell's row (written
+// by k_p2m) with float atomics.  The last block to finish clears the list's counters for the next
+// P2M; with an empty list every block leaves at once.
+template <int D, int RHO>
+__global__ void __launch_bounds__(128) k_p2m_over(const float4 *__restrict__ rec, const int *__restrict__ start,
+                                                  int n, float lo, float h, float inv_h, float *__restrict__ M,
+                                                  const int2 *__restrict__ over, unsigned long long *over_ctr) {
+    constexpr int P = ncoef(D, RHO), Pp = pad4(P);
+    const unsigned long long tot = *reinterpret_cast<volatile unsigned long long *>(over_ctr);
+    if (tot == 0) return;
+    const int nent = (int)(tot >> 32), nchunks = (int)(tot & 0xffffffffu);
+    float acc[P];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nchunks; i += gridDim.x * blockDim.x) {
+        int a = 0, b = nent;                         // over[a].y <= i < over[a + 1].y
+        while (b - a > 1) {
+            const int mid = (a + b) >> 1;
+            if (__ldg(&over[mid].y) <= i) a = mid; else b = mid;
+        }
+        const int2 ent = __ldg(&over[a]);
+        const int64_t cell = ent.x;
+        const int jc = __ldg(start + cell) + kP2MCap * (1 + i - ent.y);
+        const int jc1 = min(__ldg(start + cell + 1), jc + kP2MCap);
+        float z[3];
+        cell_centre<D>(cell, n, lo, h, z);
+#pragma unroll
+        for (int k = 0; k < P; ++k) acc[k] = 0.0f;
+        for (int j = jc; j < jc1; ++j) p2m_add<D, RHO>(acc, __ldg(rec + j), z, inv_h);
+#pragma unroll
+        for (int k = 0; k < P; ++k) atomicAdd(M + cell * Pp + k, acc[k]);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(over_ctr + 1, 1ull) == gridDim.x - 1) {   // every block has read the counters
+            over_ctr[0] = 0;
+            over_ctr[1] = 0;
+        }
+    }
 }
 
 cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w, float *M0) {
@@ -105,11 +198,21 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     const size_t smem = sizeof(float) * kP2MThreads * pl->Pp;
     const float h = (float)pl->lev[0].h, inv_h = (float)(1.0 / pl->lev[0].h);
     cudaError_t err = cudaSuccess;
-    pl->launches[FC2T2_STAGE_P2M] += 1;
+    pl->launches[FC2T2_STAGE_P2M] += 2;
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const unsigned oblocks = (unsigned)(4 * (sms > 0 ? sms : 1));
     FC2T2_DISPATCH(pl->D, pl->rho,
-                   (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.rec, w.start, pl->n, G,
-                                                                    pl->lo_f, h, inv_h, M0, pl->d_flags + 2),
-                    err = cudaGetLastError()),
+                   (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.rec, w.start, pl->n, G, pl->lo_f, h, inv_h,
+                                                                    M0, pl->d_flags + 2, pl->d_over,
+                                                                    pl->d_over_ctr),
+                    err = cudaGetLastError(),
+                    err = err != cudaSuccess ? err
+                                             : (k_p2m_over<D_, R_><<<oblocks, 128, 0, s>>>(w.rec, w.start, pl->n,
+                                                                                          pl->lo_f, h, inv_h, M0,
+                                                                                          pl->d_over, pl->d_over_ctr),
+                                                cudaGetLastError())),
                    return cudaErrorInvalidValue)
     return err;
 }

@@ -21,19 +21,33 @@ __global__ void __launch_bounds__(256) k_bin_count(const float *__restrict__ x, 
                                                    float lo, float scale, int *__restrict__ key,
                                                    int *__restrict__ rank, int *__restrict__ count,
                                                    int *__restrict__ flags) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    int lin = 0;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool live = i < n;
+    int lin = -1;                          // lanes past the end join no group of a real cell
     bool out = false;
+    if (live) {
+        lin = 0;
 #pragma unroll
-    for (int d = D - 1; d >= 0; --d) {
-        float xd = x[i * D + d];
-        out |= outside(xd, lo, scale, grid);
-        lin = lin * grid + cell_of(xd, lo, scale, grid);
+        for (int d = D - 1; d >= 0; --d) {
+            float xd = x[i * D + d];
+            out |= outside(xd, lo, scale, grid);
+            lin = lin * grid + cell_of(xd, lo, scale, grid);
+        }
     }
     if (out) atomicOr(flags, 1);
+    // lanes of the warp that fall in the same cell take one atomic together: the group's lowest
+    // lane adds the group's size, and each lane's rank is its position within the group (points
+    // that arrive in runs along a cell -- samples along a ray -- no longer serialise on one counter)
+    const unsigned peers = __match_any_sync(0xffffffffu, lin);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    const int before = __popc(peers & ((1u << lane) - 1u));
+    int base = 0;
+    if (live && lane == leader) base = atomicAdd(count + lin, __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (!live) return;
     key[i] = lin;
-    rank[i] = atomicAdd(count + lin, 1);
+    rank[i] = base + before;
 }
 
 cudaError_t launch_bin_count(const fc2t2_plan_s *pl, cudaStream_t s, const float *x, int64_t n,

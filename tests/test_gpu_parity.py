@@ -111,6 +111,33 @@ def test_grid_sizes(lib, dim, grid):
     assert_close(y, yo, what=f"D{dim} n{grid}")
 
 
+@pytest.mark.parametrize("dim,grid,order,m2l", [(3, 4, 4, "fp32"), (3, 8, 6, "separable"), (2, 8, 8, "fp32"),
+                                                (3, 8, 8, "separable")])
+def test_dense_cells(lib, dim, grid, order, m2l):
+    """Many points per finest cell (hundreds to a few thousand, well past the 32 one P2M thread
+    takes; the rest go through the overflow kernel's atomics), clustered so that a few cells hold
+    most of them; forward and backward against the oracle.  (The FP32 bar holds for sums of a few
+    thousand weights of random sign per coefficient: sqrt(n) times the unit roundoff is 4e-6 at
+    n = 4000.)"""
+    rng = np.random.default_rng(40 + dim + grid + order)
+    N, M = 12000, 9000
+    centre = rng.uniform(0.3, 0.7, size=dim)
+    p = np.clip(centre + 0.05 * rng.standard_normal((N, dim)), 0.0, 0.999).astype(np.float32)
+    p[: N // 3] = rng.random((N // 3, dim)).astype(np.float32)
+    w = rng.standard_normal(N).astype(np.float32)
+    q = np.clip(centre + 0.08 * rng.standard_normal((M, dim)), 0.0, 0.999).astype(np.float32)
+    sigma = 1.5 / grid
+    plan = make_plan(dim, grid, order, sigma, N, M, m2l=m2l)
+    y = run_forward(plan, p, w, q)
+    d = odesc(dim, grid, order, sigma)
+    assert_close(y, oracle.forward(d, *f64(p, w, q)), what=f"dense forward D{dim} n{grid} rho{order}")
+    ybar = rng.standard_normal(M).astype(np.float32)
+    wbar, pbar = run_backward(plan, p, w, q, ybar)
+    wo, po = oracle.backward(d, *f64(p, w, q, ybar))
+    assert_close(wbar, wo, what="dense wbar")
+    assert_close(pbar, po, what="dense pbar")
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_polynomial_kernel_is_exact(lib, dim):
     """For a polynomial psi of degree <= rho the series equals the direct sum of Eq. 1."""

@@ -102,6 +102,15 @@ def test_noalloc_at_its_limits(lib, dim, grid):
     assert rel_l2(y_na, planned_forward(wl)) <= REL_L2
 
 
+def test_noalloc_dense_cells(lib):
+    """65536 sources in 64 finest cells (about 1000 per cell: most go through P2M's overflow
+    kernel), against the planned forward and the oracle."""
+    wl = workloads.uniform(907, 3, 65536, 4000, 4, 4, 0.4)
+    y_na = noalloc_forward(lib, wl, None)
+    assert rel_l2(y_na, planned_forward(wl)) <= REL_L2
+    assert rel_l2(y_na, oracle_forward(wl)) <= REL_L2
+
+
 def test_noalloc_without_sources_gives_zero(lib):
     wl = workloads.uniform(906, 3, 1000, 3000, 16, 4, 0.06)
     noalloc_forward(lib, wl, None)                    # leaves nonzero coefficients in the array
