@@ -44,7 +44,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the transform's M2L launches, on
 # the same grid and order at 2^18 points: the M2L launches do not depend on the point count);
 # None where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"separable": (88.1 + 12.6 + 222.3 + 63.5 + 222.4 + 63.5 + 161.8 + 5.0 + 176.4 + 16.7 + 62.2 + 1.2) * 1e6,
+M2L_TRAFFIC_BYTES = {"separable": 1079708416.0,
                      "bf16x3": (464.0 + 82.8) * 1e6}
 
 
@@ -289,7 +289,7 @@ def measure_mode(mode, wl, args, world, dev, flush, ref=None, do_e2e=False, cloc
     _, launches = plan.profile_read(reset=True)
     total_ms = aggregate_max(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     out.ms_per_step = total_ms / nsteps
-    out.value = wl.M * nsteps * world / (total_ms / 1e3)
+    out.value = job_value(wl.M, nsteps, world, total_ms)
     out.launches = int(sum(launches.values()))
     out.launches_per_step = {k: v / nsteps for k, v in launches.items()}
     # per-stage device time from CUDA events around each stage, in separate untimed steps: with
@@ -590,104 +590,116 @@ def measure_ray_queries(args, world, dev, flush, modes=("separable", "bf16x3", "
 
 def measure_fit(dev, flush, steps, n=1 << 24, adam_steps=100, n_ref=2048, check=True):
     """The large fitting loop: 2^24 sources from 64 anisotropic Gaussians, 2^24 uniform queries,
-    128^3, order 8, sigma 0.005, mixed-precision (TF32) M2L; targets from the ground-truth set, w
-    initialised to 0.1 N(0,1) (seed 5002), Adam (lr 1e-3) on (w, p) through the autograd layer.
-    Reports one timed forward + backward step, the device memory it holds (the library's plan
-    workspace and the step's tensors; the backward rebuilds its own expansion from (q, ybar), so no
-    expansion of the forward is kept), step 0 against the oracle at `n_ref` samples, and the loss
-    over `adam_steps` steps."""
+    128^3, order 8, sigma 0.005; targets from the ground-truth set, w initialised to 0.1 N(0,1)
+    (seed 5002), Adam (lr 1e-3) on (w, p) through the autograd layer.  The configured form is the
+    mixed-precision (TF32) M2L: one timed forward + backward step, the device memory it holds (the
+    library's plan workspace and the step's tensors; the backward rebuilds its own expansion from
+    (q, ybar), so no expansion of the forward is kept), step 0 against the oracle at `n_ref`
+    samples, and the loss over `adam_steps` steps.  The FP32 separable form is timed and checked on
+    the same step 0 beside it."""
     import numpy as np
     import torch
     from paper_2111_00110_gb300 import workloads
     from paper_2111_00110_gb300.transform import Plan, fc2t2
     gt = workloads.fit_large(N=n, M=n)
-    torch.cuda.synchronize(dev)
-    free0, total = torch.cuda.mem_get_info(dev)
-    plan = Plan(3, gt.grid, gt.order, gt.sigma, m2l="tf32", max_sources=n, max_queries=n, device=dev)
-    torch.cuda.synchronize(dev)
-    free1, _ = torch.cuda.mem_get_info(dev)
     q = torch.from_numpy(gt.q).to(dev)
-    with torch.no_grad():
-        target = plan.forward(torch.from_numpy(gt.p).to(dev), torch.from_numpy(gt.w).to(dev), q)
     w0 = (0.1 * np.random.default_rng(5002).standard_normal(n)).astype(np.float32)
-    p = torch.from_numpy(gt.p).to(dev).requires_grad_(True)
-    w = torch.from_numpy(w0).to(dev).requires_grad_(True)
     stream = torch.cuda.current_stream(dev)
-
-    def loss_and_grad():
-        y = fc2t2(p, w, q, plan)
-        loss = torch.mean((y - target) ** 2)
-        loss.backward()
-        return y, loss
-
-    # step 0: the oracle check on samples, and the timed forward + backward
-    y, loss0 = loss_and_grad()
-    torch.cuda.synchronize(dev)
-    err = None
-    if check:
-        import oracle
-        d = oracle.OracleDesc(dim=3, grid=gt.grid, order=gt.order, sigma=gt.sigma)
-        rng = np.random.default_rng(7)
-        sq = np.sort(rng.choice(n, size=n_ref, replace=False))
-        sp = np.sort(rng.choice(n, size=n_ref, replace=False))
-        f64 = lambda a: np.asarray(a, dtype=np.float64)
-        yo = oracle.forward(d, f64(gt.p), f64(w0), f64(gt.q), sel=sq)
-        ybar = (2.0 / n) * (y - target).detach().cpu().numpy()
-        wo, po = oracle.backward(d, f64(gt.p), f64(w0), f64(gt.q), f64(ybar), sel=sp)
-        err = {"y": rel_l2(y.detach().cpu().numpy()[sq], yo), "wbar": rel_l2(w.grad.cpu().numpy()[sp], wo),
-               "pbar": rel_l2(p.grad.cpu().numpy()[sp], po)}
-    torch.cuda.reset_peak_memory_stats(dev)
-    for _ in range(2):
-        w.grad = None
-        p.grad = None
-        loss_and_grad()
-    torch.cuda.synchronize(dev)
-    total_ms = 0.0
-    for _ in range(steps):
-        flush.zero_()
-        w.grad = None
-        p.grad = None
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        loss_and_grad()
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        total_ms += a.elapsed_time(b)
-    ms = total_ms / steps
-    free2, _ = torch.cuda.mem_get_info(dev)
-    mem = {"plan_workspace_bytes": int(free0 - free1), "device_in_use_after_steps_bytes": int(free0 - free2),
-           "torch_peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
-           "finest_expansion_bytes": int(gt.grid ** 3 * plan.info()["coefficients"] * 4)}
-    # the loop
-    with torch.no_grad():
-        w.copy_(torch.from_numpy(w0).to(dev))
-        p.copy_(torch.from_numpy(gt.p).to(dev))
-    opt = torch.optim.Adam([w, p], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+    rng = np.random.default_rng(7)
+    sq = np.sort(rng.choice(n, size=n_ref, replace=False))
+    sp = np.sort(rng.choice(n, size=n_ref, replace=False))
+    target = None
+    ref_y = None
     hi = float(np.nextafter(np.float32(1.0), np.float32(0.0)))
-    losses = []
-    torch.cuda.synchronize(dev)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    loss_t = []
-    for _ in range(adam_steps):
-        opt.zero_grad()
-        with torch.no_grad():
-            p.clamp_(0.0, hi)
-        _, loss = loss_and_grad()
-        opt.step()
-        loss_t.append(loss.detach())
-    b.record(stream)
-    torch.cuda.synchronize(dev)
-    losses = [float(x) for x in loss_t]
-    plan.check()
-    plan.close()
-    return {"workload": "fit_large: 2^24 sources (64 anisotropic Gaussians), 2^24 uniform queries",
-            "N": n, "M": n, "grid": gt.grid, "order": gt.order, "sigma": gt.sigma, "m2l": "tf32",
-            "value": n / (ms / 1e3), "unit": "query-evals/s (fwd+bwd through the autograd layer)",
-            "ms_per_step": ms, "steps": steps, "step0_rel_l2_vs_oracle": err,
-            "memory": mem,
-            "adam": {"steps": adam_steps, "lr": 1e-3, "ms_total": a.elapsed_time(b),
-                     "loss": {str(i): losses[i] for i in range(0, adam_steps, 10)} | {str(adam_steps - 1): losses[-1]}}}
+    out = {"workload": "fit_large: 2^24 sources (64 anisotropic Gaussians), 2^24 uniform queries",
+           "N": n, "M": n, "grid": gt.grid, "order": gt.order, "sigma": gt.sigma,
+           "unit": "query-evals/s (fwd+bwd through the autograd layer)"}
+    for form in ("tf32", "separable"):
+        torch.cuda.synchronize(dev)
+        free0, _ = torch.cuda.mem_get_info(dev)
+        plan = Plan(3, gt.grid, gt.order, gt.sigma, m2l=form, max_sources=n, max_queries=n, device=dev)
+        torch.cuda.synchronize(dev)
+        free1, _ = torch.cuda.mem_get_info(dev)
+        if target is None:
+            # targets: the configured (TF32) transform of the ground-truth set
+            with torch.no_grad():
+                target = plan.forward(torch.from_numpy(gt.p).to(dev), torch.from_numpy(gt.w).to(dev), q)
+        p = torch.from_numpy(gt.p).to(dev).requires_grad_(True)
+        w = torch.from_numpy(w0).to(dev).requires_grad_(True)
+
+        def loss_and_grad():
+            y = fc2t2(p, w, q, plan)
+            loss = torch.mean((y - target) ** 2)
+            loss.backward()
+            return y, loss
+
+        y, _ = loss_and_grad()
+        torch.cuda.synchronize(dev)
+        err = None
+        if check:
+            import oracle
+            d = oracle.OracleDesc(dim=3, grid=gt.grid, order=gt.order, sigma=gt.sigma)
+            f64 = lambda a: np.asarray(a, dtype=np.float64)
+            if ref_y is None:
+                ref_y = oracle.forward(d, f64(gt.p), f64(w0), f64(gt.q), sel=sq)
+            ybar = (2.0 / n) * (y - target).detach().cpu().numpy()
+            # (the cotangent depends on the form's own y: the backward reference is per form)
+            wo, po = oracle.backward(d, f64(gt.p), f64(w0), f64(gt.q), f64(ybar), sel=sp)
+            err = {"y": rel_l2(y.detach().cpu().numpy()[sq], ref_y), "wbar": rel_l2(w.grad.cpu().numpy()[sp], wo),
+                   "pbar": rel_l2(p.grad.cpu().numpy()[sp], po)}
+        torch.cuda.reset_peak_memory_stats(dev)
+        for _ in range(2):
+            w.grad = None
+            p.grad = None
+            loss_and_grad()
+        torch.cuda.synchronize(dev)
+        total_ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            w.grad = None
+            p.grad = None
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            loss_and_grad()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            total_ms += a.elapsed_time(b)
+        ms = total_ms / steps
+        free2, _ = torch.cuda.mem_get_info(dev)
+        res = {"m2l": form, "value": n / (ms / 1e3), "ms_per_step": ms, "steps": steps,
+               "step0_rel_l2_vs_oracle": err,
+               "memory": {"plan_workspace_bytes": int(free0 - free1),
+                          "device_in_use_after_steps_bytes": int(free0 - free2),
+                          "torch_peak_allocated_bytes": int(torch.cuda.max_memory_allocated(dev)),
+                          "finest_expansion_bytes": int(gt.grid ** 3 * plan.info()["coefficients"] * 4)}}
+        if form == "tf32":
+            with torch.no_grad():
+                w.copy_(torch.from_numpy(w0).to(dev))
+                p.copy_(torch.from_numpy(gt.p).to(dev))
+            opt = torch.optim.Adam([w, p], lr=1e-3, betas=(0.9, 0.999), eps=1e-8)
+            loss_t = []
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(adam_steps):
+                opt.zero_grad()
+                with torch.no_grad():
+                    p.clamp_(0.0, hi)
+                _, loss = loss_and_grad()
+                opt.step()
+                loss_t.append(loss.detach())
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            losses = [float(x) for x in loss_t]
+            res["adam"] = {"steps": adam_steps, "lr": 1e-3, "ms_total": a.elapsed_time(b),
+                           "loss": {str(i): losses[i] for i in range(0, adam_steps, 10)} | {str(adam_steps - 1): losses[-1]}}
+            out.update(res)
+        else:
+            out["fp32_separable"] = res
+        plan.check()
+        plan.close()
+        del p, w
+    return out
 
 
 def measure_batched(dev, flush, steps, warmup, n_inst=64):
@@ -753,6 +765,18 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
             "one_stream": {"ms_per_step": ms_seq, "value": queries / (ms_seq / 1e3)}}
 
 
+def replica_workload(rank: int, **sizes):
+    """The benchmark workload of one rank: weak scaling, every rank transforms its own
+    independent point set (the uniform3d recipe drawn with seed 2 + rank)."""
+    from paper_2111_00110_gb300 import workloads
+    return workloads.uniform3d(seed=2 + rank, **sizes)
+
+
+def job_value(units_per_rank: int, steps: int, world: int, job_ms: float) -> float:
+    """Whole-job throughput: the units of every rank over the slowest rank's time."""
+    return units_per_rank * steps * world / (job_ms / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
 
@@ -763,7 +787,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     # weak scaling: every rank transforms its own independent point set
-    wl = workloads.uniform3d(seed=2 + rank)
+    wl = replica_workload(rank)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
     ref = None
     if not args.no_check and rank == 0:

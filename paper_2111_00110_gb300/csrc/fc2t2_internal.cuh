@@ -68,6 +68,23 @@ __device__ __forceinline__ void power_ladder(float u, float (&pw)[RHO + 1]) {
     for (int k = 1; k <= RHO; ++k) pw[k] = pw[k - 1] * (u * (1.0f / (float)k));
 }
 
+// u^k for k = 0..RHO (one multiply per power; the factorials are applied once per row instead)
+template <int RHO>
+__device__ __forceinline__ void powers(float u, float (&pw)[RHO + 1]) {
+    pw[0] = 1.0f;
+#pragma unroll
+    for (int k = 1; k <= RHO; ++k) pw[k] = pw[k - 1] * u;
+}
+
+// 1 / (a0! a1! a2!) in FP32 (a compile-time constant where the exponents are)
+__host__ __device__ constexpr float inv_fact3(int a0, int a1, int a2) {
+    double f = 1.0;
+    for (int i = 2; i <= a0; ++i) f *= i;
+    for (int i = 2; i <= a1; ++i) f *= i;
+    for (int i = 2; i <= a2; ++i) f *= i;
+    return (float)(1.0 / f);
+}
+
 // The series of one coefficient row at u (power ladders pw): value, and with GRAD the three
 // sums of the shifted rows sum_k Lt(k + e_i) u^k / k! (the gradient in u), nested over the
 // exponents; the results are added to value, g[].

@@ -441,6 +441,7 @@ __global__ void __launch_bounds__(kSepThreads, (RHO <= 6 || (AXIS == 2 && FINEST
     // stage the input rows of sources t0 - HALO .. t0 + nt + HALO - 1 (zero outside the grid): a
     // warp per row, lanes across the row (coalesced scalar loads, conflict-free stores into the odd-pitch
     // rows), kStageRows rows per warp in flight
+    bool nonzero = false;              // any staged input value nonzero (the CTA's outputs depend on no other)
     {
         constexpr int W = kSepThreads / 32, CPL = (Pt::in + 31) / 32;   // columns per lane
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -460,6 +461,7 @@ __global__ void __launch_bounds__(kSepThreads, (RHO <= 6 || (AXIS == 2 && FINEST
                     for (int k = 0; k < CPL; ++k) {
                         const int c = lane + 32 * k;
                         buf[u][k] = (ok && c < Pt::in) ? __ldg(g + c) : 0.0f;
+                        if (AXIS == 0) nonzero |= buf[u][k] != 0.0f;
                     }
                 }
 #pragma unroll
@@ -475,7 +477,30 @@ __global__ void __launch_bounds__(kSepThreads, (RHO <= 6 || (AXIS == 2 && FINEST
             }
         }
     }
-    __syncthreads();
+    // Pass X: a segment whose staged moments are all zero (no source within the windows of its
+    // targets -- much of the grid for clustered points) has zero outputs: write them and skip the
+    // arithmetic.  (Passes Y and Z read the window-dilated outputs of the pass before, which are
+    // zero on few whole segments; they skip the test.)
+    if (AXIS != 0) __syncthreads();
+    else if (!__syncthreads_or(nonzero)) {
+        constexpr int W = kSepThreads / 32, CPL = (Pt::out + 31) / 32;
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        constexpr int NOUT = (TWO_OUT || NCHAIN > 1) ? 2 : 1;
+#pragma unroll 1
+        for (int o = 0; o < NOUT; ++o) {
+            float *gout = o == 0 ? lv.out0 : lv.out1;
+#pragma unroll 1
+            for (int rr = warp; rr < nt; rr += W) {
+                float *g0 = gout + (base + (int64_t)(t0 + rr) * stride) * Pt::out;
+#pragma unroll
+                for (int k = 0; k < CPL; ++k) {
+                    const int c = lane + 32 * k;
+                    if (c < Pt::out) g0[c] = 0.0f;
+                }
+            }
+        }
+        return;
+    }
 
     // finest level: target pairs (2 tp, 2 tp + 1) of the segment (t0 and nt are even); a warp's
     // lanes cover 32 / np task slots, whose pairs the table groups by budget.  Above it: one

@@ -28,13 +28,14 @@ constexpr int kP2MThreads = 64;
 // the cell's row with float atomics.  So no thread waits on a cell much fuller than the mean.
 constexpr int kP2MCap = 32;
 
-// acc += w u^b / b! for one point (u = (x - z) / h per dimension)
+// acc += w u^b for one point (u = (x - z) / h per dimension); the factor 1 / b! is applied to the
+// finished sums (p2m_scale)
 template <int D, int RHO>
 __device__ __forceinline__ void p2m_add(float (&acc)[ncoef(D, RHO)], const float4 r, const float (&z)[3], float inv_h) {
     const float xj[3] = {r.x, r.y, r.z};
     float pw[3][RHO + 1];
 #pragma unroll
-    for (int d = 0; d < D; ++d) power_ladder<RHO>((xj[d] - z[d]) * inv_h, pw[d]);
+    for (int d = 0; d < D; ++d) powers<RHO>((xj[d] - z[d]) * inv_h, pw[d]);
     const float wj = r.w;
 #pragma unroll
     for (int a0 = 0; a0 <= RHO; ++a0) {
@@ -53,6 +54,34 @@ __device__ __forceinline__ void p2m_add(float (&acc)[ncoef(D, RHO)], const float
                 }
             }
         }
+    }
+}
+
+// acc(b) *= 1 / b!
+template <int D, int RHO>
+__device__ __forceinline__ void p2m_scale(float (&acc)[ncoef(D, RHO)]) {
+#pragma unroll
+    for (int a0 = 0; a0 <= RHO; ++a0)
+#pragma unroll
+        for (int a1 = 0; a0 + a1 <= RHO; ++a1) {
+            if (D == 2) {
+                acc[gidx2(a0, a1)] *= inv_fact3(a0, a1, 0);
+            } else {
+#pragma unroll
+                for (int a2 = 0; a0 + a1 + a2 <= RHO; ++a2) acc[gidx3(a0, a1, a2)] *= inv_fact3(a0, a1, a2);
+            }
+        }
+}
+
+// the records of [j0, j1) (j0 < j1) through f, the next record's load issued before each point's
+// arithmetic
+template <typename F>
+__device__ __forceinline__ void walk_records(const float4 *__restrict__ rec, int j0, int j1, F f) {
+    float4 r = __ldg(rec + j0);
+    for (int j = j0; j < j1; ++j) {
+        const float4 nx = j + 1 < j1 ? __ldg(rec + j + 1) : r;
+        f(r);
+        r = nx;
     }
 }
 
@@ -105,6 +134,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
             const float4 r = (have && j - jb0 < nst) ? smem4[j - jb0] : __ldg(rec + j);
             p2m_add<D, RHO>(acc, r, z, inv_h);
         }
+        p2m_scale<D, RHO>(acc);
     }
     __syncthreads();   // every staged record has been read before the buffer takes the output rows
 #pragma unroll
@@ -178,7 +208,8 @@ __global__ void __launch_bounds__(128) k_p2m_over(const float4 *__restrict__ rec
         cell_centre<D>(cell, n, lo, h, z);
 #pragma unroll
         for (int k = 0; k < P; ++k) acc[k] = 0.0f;
-        for (int j = jc; j < jc1; ++j) p2m_add<D, RHO>(acc, __ldg(rec + j), z, inv_h);
+        walk_records(rec, jc, jc1, [&](const float4 r) { p2m_add<D, RHO>(acc, r, z, inv_h); });
+        p2m_scale<D, RHO>(acc);
 #pragma unroll
         for (int k = 0; k < P; ++k) atomicAdd(M + cell * Pp + k, acc[k]);
     }
