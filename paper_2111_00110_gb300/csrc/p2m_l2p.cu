@@ -24,9 +24,12 @@ namespace fc2t2 {
 constexpr int kP2MThreads = 64;
 // A P2M thread takes at most kP2MCap points of its cell; the points of a cell beyond its first
 // kP2MCap (clustered sources, or the many samples of rays that cross a cell) are summed by a second
-// kernel, in chunks of kP2MCap consecutive sorted points spread over the whole GPU, and added to
+// kernel, in chunks of kOverChunk consecutive sorted points spread over the whole GPU, and added to
 // the cell's row with float atomics.  So no thread waits on a cell much fuller than the mean.
 constexpr int kP2MCap = 32;
+// points per overflow chunk: one thread sums a chunk and adds it to its cell's row with one row of
+// atomics, so longer chunks mean fewer atomics on the rows of the fullest cells
+constexpr int kOverChunk = 128;
 
 // acc += w u^b for one point (u = (x - z) / h per dimension); the factor 1 / b! is applied to the
 // finished sums (p2m_scale)
@@ -147,10 +150,10 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
 
     // The cells of the block with points beyond their first kP2MCap append themselves to the
     // plan's overflow list: one 64-bit atomic per block reserves (entries, chunks) -- entry =
-    // (cell, index of its first chunk of kP2MCap points in the list's chunk numbering) -- so the
+    // (cell, index of its first chunk of kOverChunk points in the list's chunk numbering) -- so the
     // entries come out ordered by chunk index.  k_p2m_over sums the chunks.
     const int cnt = c < G ? start[c + 1] - start[c] : 0;
-    const int nch = cnt > kP2MCap ? (cnt - 1) / kP2MCap : 0;        // chunks past the first kP2MCap
+    const int nch = cnt > kP2MCap ? (cnt - kP2MCap + kOverChunk - 1) / kOverChunk : 0;   // chunks past the first kP2MCap
     if (!__syncthreads_or(nch > 0)) return;
     __shared__ int s_warp[kP2MThreads / 32][2];
     __shared__ unsigned long long s_base;
@@ -181,7 +184,7 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
 }
 
 // The overflow chunks of one P2M: a grid-stride loop over the list's chunks; chunk i belongs to the
-// last entry whose first chunk is <= i (binary search), and covers kP2MCap consecutive sorted
+// last entry whose first chunk is <= i (binary search), and covers kOverChunk consecutive sorted
 // points of that cell past its first kP2MCap.  Each chunk's sum is added to the cell's row (written
 // by k_p2m) with float atomics.  The last block to finish clears the list's counters for the next
 // P2M; with an empty list every block leaves at once.
@@ -202,8 +205,8 @@ __global__ void __launch_bounds__(128) k_p2m_over(const float4 *__restrict__ rec
         }
         const int2 ent = __ldg(&over[a]);
         const int64_t cell = ent.x;
-        const int jc = __ldg(start + cell) + kP2MCap * (1 + i - ent.y);
-        const int jc1 = min(__ldg(start + cell + 1), jc + kP2MCap);
+        const int jc = __ldg(start + cell) + kP2MCap + kOverChunk * (i - ent.y);
+        const int jc1 = min(__ldg(start + cell + 1), jc + kOverChunk);
         float z[3];
         cell_centre<D>(cell, n, lo, h, z);
 #pragma unroll
