@@ -138,6 +138,26 @@ def test_dense_cells(lib, dim, grid, order, m2l):
     assert_close(pbar, po, what="dense pbar")
 
 
+def test_dense_and_sparse_calls_alternate(lib):
+    """One plan, calls whose P2M needs the overflow list (dense cells) alternating with calls that
+    leave it empty: the list's counters are cleared between calls, so every result matches the
+    oracle."""
+    rng = np.random.default_rng(77)
+    dim, grid, order, sigma, N, M = 3, 8, 5, 0.2, 8000, 3000
+    dense = np.clip(0.5 + 0.04 * rng.standard_normal((N, dim)), 0.0, 0.999).astype(np.float32)
+    sparse = rng.random((N, dim)).astype(np.float32)
+    w = rng.standard_normal(N).astype(np.float32)
+    q = rng.random((M, dim)).astype(np.float32)
+    plan = make_plan(dim, grid, order, sigma, N, M, m2l="separable")
+    d = odesc(dim, grid, order, sigma)
+    for p in (dense, sparse, dense, sparse):
+        y = run_forward(plan, p, w, q)
+        assert_close(y, oracle.forward(d, *f64(p, w, q)), what="alternating forward")
+    ybar = rng.standard_normal(M).astype(np.float32)
+    wbar, _ = run_backward(plan, dense, w, q, ybar)
+    assert_close(wbar, oracle.backward(d, *f64(dense, w, q, ybar))[0], what="alternating wbar")
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_polynomial_kernel_is_exact(lib, dim):
     """For a polynomial psi of degree <= rho the series equals the direct sum of Eq. 1."""
