@@ -129,6 +129,69 @@ __device__ __forceinline__ void series_add(const float *Lv, const float (&pw)[3]
     g[2] += g2;
 }
 
+// series_add for two points on the same coefficient row: each coefficient is read once and feeds
+// both points' sums (the row's reads are shared, and the two points' FMA chains interleave).
+template <int D, int RHO, bool GRAD>
+__device__ __forceinline__ void series_add2(const float *Lv, const float (&pa)[3][RHO + 1], const float (&pb)[3][RHO + 1],
+                                            float &va, float (&ga)[3], float &vb, float (&gb)[3]) {
+    float a_val = 0.0f, a0g = 0.0f, a1g = 0.0f, a2g = 0.0f;
+    float b_val = 0.0f, b0g = 0.0f, b1g = 0.0f, b2g = 0.0f;
+#pragma unroll
+    for (int a0 = 0; a0 <= RHO; ++a0) {
+        float Ua = 0.0f, U1a = 0.0f, U2a = 0.0f, Ub = 0.0f, U1b = 0.0f, U2b = 0.0f;
+#pragma unroll
+        for (int a1 = 0; a1 <= RHO; ++a1) {
+            if (a0 + a1 > RHO) continue;
+            float Ta = 0.0f, T2a = 0.0f, Tb = 0.0f, T2b = 0.0f;
+            if (D == 2) {
+                Ta = Tb = Lv[gidx2(a0, a1)];
+            } else {
+#pragma unroll
+                for (int a2 = 0; a2 <= RHO; ++a2) {
+                    if (a0 + a1 + a2 > RHO) continue;
+                    const float l = Lv[gidx3(a0, a1, a2)];
+                    Ta = fmaf(pa[2][a2], l, Ta);
+                    Tb = fmaf(pb[2][a2], l, Tb);
+                    if (GRAD && a2 >= 1) {
+                        T2a = fmaf(pa[2][a2 - 1], l, T2a);
+                        T2b = fmaf(pb[2][a2 - 1], l, T2b);
+                    }
+                }
+            }
+            Ua = fmaf(pa[1][a1], Ta, Ua);
+            Ub = fmaf(pb[1][a1], Tb, Ub);
+            if (GRAD) {
+                if (a1 >= 1) {
+                    U1a = fmaf(pa[1][a1 - 1], Ta, U1a);
+                    U1b = fmaf(pb[1][a1 - 1], Tb, U1b);
+                }
+                if (D == 3) {
+                    U2a = fmaf(pa[1][a1], T2a, U2a);
+                    U2b = fmaf(pb[1][a1], T2b, U2b);
+                }
+            }
+        }
+        a_val = fmaf(pa[0][a0], Ua, a_val);
+        b_val = fmaf(pb[0][a0], Ub, b_val);
+        if (GRAD) {
+            if (a0 >= 1) {
+                a0g = fmaf(pa[0][a0 - 1], Ua, a0g);
+                b0g = fmaf(pb[0][a0 - 1], Ub, b0g);
+            }
+            a1g = fmaf(pa[0][a0], U1a, a1g);
+            b1g = fmaf(pb[0][a0], U1b, b1g);
+            if (D == 3) {
+                a2g = fmaf(pa[0][a0], U2a, a2g);
+                b2g = fmaf(pb[0][a0], U2b, b2g);
+            }
+        }
+    }
+    va += a_val;
+    ga[0] += a0g; ga[1] += a1g; ga[2] += a2g;
+    vb += b_val;
+    gb[0] += b0g; gb[1] += b1g; gb[2] += b2g;
+}
+
 // One counting sort of points into finest-level cells.
 struct SortWork {
     int64_t cap = 0;

@@ -273,6 +273,39 @@ __device__ __forceinline__ void l2p_store(int64_t i, float value, const float (&
     }
 }
 
+// The series of staged rows ra and rb (row index in units of P4 float4) at two points, into
+// (va, ga) and (vb, gb); one shared pass over the row when both points use the same row.
+template <int D, int RHO, bool GRAD>
+__device__ __forceinline__ void l2p_rows(const float4 *rows, int P4, int ra, int rb, bool hasb,
+                                         const float (&pa)[3][RHO + 1], const float (&pb)[3][RHO + 1], float &va,
+                                         float (&ga)[3], float &vb, float (&gb)[3]) {
+    constexpr int Pp = pad4(ncoef(D, RHO));
+    float Lv[Pp];
+    if (hasb && ra == rb) {
+#pragma unroll
+        for (int i = 0; i < Pp / 4; ++i) {
+            const float4 v = rows[ra * P4 + i];
+            Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
+        }
+        series_add2<D, RHO, GRAD>(Lv, pa, pb, va, ga, vb, gb);
+        return;
+    }
+#pragma unroll
+    for (int i = 0; i < Pp / 4; ++i) {
+        const float4 v = rows[ra * P4 + i];
+        Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
+    }
+    series_add<D, RHO, GRAD>(Lv, pa, va, ga);
+    if (hasb) {
+#pragma unroll
+        for (int i = 0; i < Pp / 4; ++i) {
+            const float4 v = rows[rb * P4 + i];
+            Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
+        }
+        series_add<D, RHO, GRAD>(Lv, pb, vb, gb);
+    }
+}
+
 // L2P, staged: a CTA owns SC = min(32, n) consecutive finest cells of one x-line.  Their
 // coefficient rows are contiguous in memory and are copied to shared memory with coalesced
 // 16-byte loads (all in flight at once); the CTA then walks the cell-sorted points of those cells
@@ -331,68 +364,91 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
         tc::bulk_g2s(rows, L0 + c0 * Pp, b0, &staged);
         if (TWO) tc::bulk_g2s(rows + sc * P4, L1 + p0 * Pp, b1, &staged);
     }
-    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
-    int in = 0;                                            // and its place in the input order
-    if (j0 + (int)threadIdx.x < j1) {
-        rn = __ldg(rec + j0 + threadIdx.x);
-        in = __ldg(perm + j0 + threadIdx.x);
+    // Without the parent rows (TWO false: many targets per cell) a thread takes two consecutive
+    // sorted points per round -- mostly of one cell, whose series then share each row read; with
+    // them (few targets per cell) one point, so that the CTA's threads all have work.  Records are
+    // loaded one round ahead.
+    constexpr int NPT = TWO ? 1 : 2;
+    float4 rn[NPT];
+    int in[NPT];                                           // and their places in the input order
+#pragma unroll
+    for (int u = 0; u < NPT; ++u) {
+        rn[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+        in[u] = 0;
+        if (j0 + NPT * (int)threadIdx.x + u < j1) {
+            rn[u] = __ldg(rec + j0 + NPT * threadIdx.x + u);
+            in[u] = __ldg(perm + j0 + NPT * threadIdx.x + u);
+        }
     }
     if (!tc::mbar_wait(&staged, 0, err, 512)) return;     // (bounded; a timeout is reported by the plan)
-    for (int j = j0 + threadIdx.x; j < j1; j += kL2PThreads) {
-        const float4 r = rn;
-        const int i_out = in;
-        if (j + kL2PThreads < j1) {   // the next record, one round ahead
-            rn = __ldg(rec + j + kL2PThreads);
-            in = __ldg(perm + j + kL2PThreads);
-        }
-        const float xj[3] = {r.x, r.y, r.z};
-        int cd[3];
+    for (int j = j0 + NPT * (int)threadIdx.x; j < j1; j += NPT * kL2PThreads) {
+        const bool hasb = NPT == 2 && j + 1 < j1;
+        float4 r[NPT];
+        int i_out[NPT];
 #pragma unroll
-        for (int d = 0; d < D; ++d) cd[d] = cell_of(xj[d], lo, scale, n);   // the sort's binning rule
-        // the point's cell is in the segment (the sort used the same rule); clamped all the same
-        int lx = cd[0] - x0;
-        lx = lx < 0 ? 0 : (lx >= sc ? sc - 1 : lx);
-        float value = 0.0f, g[3] = {0.0f, 0.0f, 0.0f};
-        {
-            float pw[3][RHO + 1];
+        for (int u = 0; u < NPT; ++u) {
+            r[u] = rn[u];
+            i_out[u] = in[u];
+            if (j + NPT * kL2PThreads + u < j1) {   // the next records, one round ahead
+                rn[u] = __ldg(rec + j + NPT * kL2PThreads + u);
+                in[u] = __ldg(perm + j + NPT * kL2PThreads + u);
+            }
+        }
+        int cd[NPT][3], lx[NPT];
+        float pw[NPT][3][RHO + 1];
+#pragma unroll
+        for (int u = 0; u < NPT; ++u) {
+            const float xj[3] = {r[u].x, r[u].y, r[u].z};
+#pragma unroll
+            for (int d = 0; d < D; ++d) cd[u][d] = cell_of(xj[d], lo, scale, n);   // the sort's binning rule
+            // the point's cell is in the segment (the sort used the same rule); clamped all the same
+            const int l = cd[u][0] - x0;
+            lx[u] = l < 0 ? 0 : (l >= sc ? sc - 1 : l);
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                const float z = lo + ((float)cd[d] + 0.5f) * h0;
-                power_ladder<RHO>((xj[d] - z) * inv_h0, pw[d]);
+                const float z = lo + ((float)cd[u][d] + 0.5f) * h0;
+                power_ladder<RHO>((xj[d] - z) * inv_h0, pw[u][d]);
             }
+        }
+        float value[2] = {0.0f, 0.0f}, g[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+        if constexpr (NPT == 2) {
+            l2p_rows<D, RHO, GRAD>(rows, P4, lx[0], lx[1], hasb, pw[0], pw[1], value[0], g[0], value[1], g[1]);
+        } else {
             float Lv[Pp];
 #pragma unroll
             for (int i = 0; i < P4; ++i) {
-                const float4 v = rows[lx * P4 + i];
+                const float4 v = rows[lx[0] * P4 + i];
                 Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
             }
-            series_add<D, RHO, GRAD>(Lv, pw, value, g);
+            series_add<D, RHO, GRAD>(Lv, pw[0], value[0], g[0]);
         }
-        float scale_g = r.w * inv_h0;
         if (TWO) {
-            float pw[3][RHO + 1];
+            // level 1's complete series about the parent cell (x0 is even): one point a thread
+            const float xj[3] = {r[0].x, r[0].y, r[0].z};
+            float pw1[3][RHO + 1];
 #pragma unroll
             for (int d = 0; d < D; ++d) {
-                const float z = lo + ((float)(cd[d] >> 1) + 0.5f) * h1;
-                power_ladder<RHO>((xj[d] - z) * inv_h1, pw[d]);
+                const float z = lo + ((float)(cd[0][d] >> 1) + 0.5f) * h1;
+                power_ladder<RHO>((xj[d] - z) * inv_h1, pw1[d]);
             }
             float Lv[Pp];
-            const int px = lx >> 1;   // x0 is even
+            const int px = lx[0] >> 1;
 #pragma unroll
             for (int i = 0; i < P4; ++i) {
                 const float4 v = rows[(sc + px) * P4 + i];
                 Lv[4 * i] = v.x; Lv[4 * i + 1] = v.y; Lv[4 * i + 2] = v.z; Lv[4 * i + 3] = v.w;
             }
             float v1 = 0.0f, g1[3] = {0.0f, 0.0f, 0.0f};
-            series_add<D, RHO, GRAD>(Lv, pw, v1, g1);
-            value += v1;
+            series_add<D, RHO, GRAD>(Lv, pw1, v1, g1);
+            value[0] += v1;
             if (GRAD) {
                 // both gradients in x: the finest part scaled by 1/h0, level 1's by 1/h1
 #pragma unroll
-                for (int d = 0; d < 3; ++d) g[d] = fmaf(inv_h1 / inv_h0, g1[d], g[d]);
+                for (int d = 0; d < 3; ++d) g[0][d] = fmaf(inv_h1 / inv_h0, g1[d], g[0][d]);
             }
         }
-        l2p_store<D, GRAD>(i_out, value, g, scale_g, val, grad, accumulate);
+        l2p_store<D, GRAD>(i_out[0], value[0], g[0], r[0].w * inv_h0, val, grad, accumulate);
+        if (NPT == 2 && hasb) l2p_store<D, GRAD>(i_out[NPT - 1], value[1], g[1], r[NPT - 1].w * inv_h0, val, grad, accumulate);
     }
 }
 
