@@ -19,11 +19,14 @@
 // with kx + by + bz + e <= rho and kx + ky + bz + e' <= rho.  A 4-indexed row holds C(rho+4, 4)
 // values (210 at order 6), grouped by its two leading indices; each group is a triangle.
 //
-// Every pass is a line convolution: a CTA stages a segment of one grid line (up to 32 target
-// cells plus the source cells their windows reach: 2 on the low side, 2 on the high side) of its
-// input rows in shared memory with coalesced loads, computes its outputs from shared memory (a
-// thread per pair of targets and task), and writes the segment's output rows coalesced.  The passes move far fewer bytes and flops than the dense M2L, so they are bound by
-// HBM bandwidth; all levels of one pass run in one launch.
+// Every pass is a line convolution: a CTA stages a segment of one grid line (up to 64 target
+// cells at the finest level, 32 above it, plus the source cells their windows reach: 2 on each
+// side at the finest level, 3 above it) of its input rows in shared memory with coalesced loads,
+// computes its outputs from shared memory (a thread per pair of targets and task at the finest
+// level, per target and task above it), and writes the segment's output rows coalesced.  The
+// passes move far fewer flops than the dense M2L; their cost is instruction issue and the
+// intermediate rows' memory traffic.  The finest level runs in one launch per pass, the levels
+// above it in another.
 #include <algorithm>
 #include <cstring>
 
@@ -616,18 +619,22 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
                 pl->sep.t_off[l][buf][chain] = off;
                 off += pl->lev[l].G * Q4p;
             }
-    // segment length per level: the longest of 32, 16, 8, 4 cells that keeps every pass's CTA
-    // within 116 KB of shared memory (segments shorter than a warp split warps between tasks)
+    // segment length per level: the longest of 64 (finest level only: a warp's lanes then hold its
+    // 32 target pairs), 32, 16, 8, 4 cells that keeps every pass's CTA within 116 KB of shared
+    // memory at orders <= 6 (two or three CTAs per multiprocessor) and 220 KB at orders 7-8 (one:
+    // there the longer segments' smaller halo share outweighs the lost CTA, order 8 M2L 2.99 ->
+    // 2.72 ms per step); segments shorter than a warp split warps between tasks
     size_t max_smem = 0;
+    const size_t cap = (size_t)(pl->rho >= 7 ? 220 : 116) * 1024;
     for (int l = 0; l < pl->nlev; ++l) {
         const int n = pl->lev[l].n;
         int seg = 4;
-        for (int cand : {32, 16, 8}) {
-            if (cand > n) continue;
+        for (int cand : {64, 32, 16, 8}) {
+            if (cand > n || (cand == 64 && l != 0)) continue;
             bool fits = true;
             for (int axis = 0; axis < 3; ++axis) {
                 const int ip = axis == 0 ? pl->Pp : Q4p, op = axis == 2 ? pl->Pp : Q4p;
-                if (sep_smem(axis, cand, l == 0, ip, op) > 116 * 1024) fits = false;
+                if (sep_smem(axis, cand, l == 0, ip, op) > cap) fits = false;
             }
             if (fits) { seg = cand; break; }
         }
