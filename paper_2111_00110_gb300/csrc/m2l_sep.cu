@@ -35,7 +35,10 @@
 
 namespace fc2t2 {
 
-constexpr int kSepThreads = 256;
+// threads per CTA: 512 at orders 7-8, whose passes run one long-segment CTA per multiprocessor
+// (more warps to hide latency: order-8 M2L 2.72 -> 2.55 ms per step), 256 below (at order 6, 512
+// threads cost 14 % of the step)
+__host__ __device__ constexpr int sep_threads(int rho) { return rho >= 7 ? 512 : 256; }
 constexpr int kStageRows = 4;   // input rows a warp loads at once while staging
 
 __host__ __device__ constexpr int q4count(int rho) { return (rho + 1) * (rho + 2) * (rho + 3) * (rho + 4) / 24; }
@@ -401,10 +404,11 @@ struct SepPitch {
     static constexpr int sin = odd_pitch(in), sout = odd_pitch(out);                 // shared-memory row
 };
 
-// Three CTAs per multiprocessor where the registers allow it without spilling (orders <= 6, and
-// the finest pass Z at orders 7-8); two elsewhere.
+// Three CTAs of 256 threads per multiprocessor at orders <= 6 (registers permitting, without
+// spills); one CTA of 512 threads at orders 7-8 (their long segments' shared memory).
 template <int RHO, int AXIS, bool FINEST>
-__global__ void __launch_bounds__(kSepThreads, (RHO <= 6 || (AXIS == 2 && FINEST)) ? 3 : 2) k_m2l_sep(const SepArgs args) {
+__global__ void __launch_bounds__(sep_threads(RHO), RHO >= 7 ? 1 : 3) k_m2l_sep(const SepArgs args) {
+    constexpr int kSepThreads = sep_threads(RHO);
     constexpr int P = ncoef(3, RHO);
     using Pt = SepPitch<RHO, AXIS>;
     constexpr bool TWO_IN = !FINEST && AXIS > 0;
@@ -665,7 +669,7 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
 }
 
 // The launch's small tables: each level's dt_o(j); the group offsets of the 4-indexed rows; the
-// task pairs (i, j) by slot, dealt to the kSepThreads / 32 warps as below.
+// task pairs (i, j) by slot, dealt to the sep_threads(rho) / 32 warps as below.
 static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_end, int axis) {
     const int rho = pl->rho;
     for (int l = l_begin; l < l_end; ++l)
@@ -687,7 +691,7 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
     // by equal budget (lanes of different budgets would run one after the other), and the groups
     // are dealt longest first to the warp with the least work so far -- the CTA's compute phase
     // ends with its busiest warp.  Unfilled slots hold (-1, -1).
-    constexpr int W = kSepThreads / 32;
+    const int W = sep_threads(pl->rho) / 32;
     const int seg = std::min(pl->sep.seg[l_begin], pl->lev[l_begin].n);
     const int G = std::max(1, (l_begin == 0 ? 64 : 32) / seg);
     struct Group { int cost; std::vector<int2> pairs; };
@@ -755,7 +759,7 @@ template <int RHO, int AXIS, bool FINEST>
 static cudaError_t sep_launch(const SepArgs &a, unsigned blocks, size_t smem, cudaStream_t s) {
     auto *fn = k_m2l_sep<RHO, AXIS, FINEST>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    fn<<<blocks, kSepThreads, smem, s>>>(a);
+    fn<<<blocks, sep_threads(RHO), smem, s>>>(a);
     return cudaGetLastError();
 }
 
