@@ -39,7 +39,15 @@ namespace fc2t2 {
 // (more warps to hide latency: order-8 M2L 2.72 -> 2.55 ms per step), 256 below (at order 6, 512
 // threads cost 14 % of the step)
 __host__ __device__ constexpr int sep_threads(int rho) { return rho >= 7 ? 512 : 256; }
-constexpr int kStageRows = 4;   // input rows a warp loads at once while staging
+// input rows a warp loads at once while staging.  At orders <= 6, enough for one round (segments
+// of up to 64 cells plus 2 halo cells on each side at the finest level, 32 plus 3 above it): every
+// warp issues all of its loads before the first one returns (order-6 M2L 0.923 -> 0.876 ms per
+// step against four rows a round).  At orders 7-8 the 16 warps of a CTA load four rows a round,
+// one round but for the last four rows of a 64-cell segment (five rows each, order-8 M2L was
+// 1.7 % slower: more registers at one CTA per multiprocessor).
+__host__ __device__ constexpr int stage_rows(int rho, bool finest) {
+    return rho >= 7 ? 4 : ((finest ? 68 : 38) + sep_threads(rho) / 32 - 1) / (sep_threads(rho) / 32);
+}
 
 __host__ __device__ constexpr int q4count(int rho) { return (rho + 1) * (rho + 2) * (rho + 3) * (rho + 4) / 24; }
 __host__ __device__ constexpr int tri_count(int r) { return (r + 1) * (r + 2) / 2; }
@@ -447,17 +455,18 @@ __global__ void __launch_bounds__(sep_threads(RHO), RHO >= 7 ? 1 : 3) k_m2l_sep(
 
     // stage the input rows of sources t0 - HALO .. t0 + nt + HALO - 1 (zero outside the grid): a
     // warp per row, lanes across the row (coalesced scalar loads, conflict-free stores into the odd-pitch
-    // rows), kStageRows rows per warp in flight
+    // rows), stage_rows(RHO, FINEST) rows per warp in flight
     bool nonzero = false;              // any staged input value nonzero (the CTA's outputs depend on no other)
     {
         constexpr int W = kSepThreads / 32, CPL = (Pt::in + 31) / 32;   // columns per lane
+        constexpr int kStageRows = stage_rows(RHO, FINEST);
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll 1
         for (int src = 0; src < (TWO_IN ? 2 : 1); ++src) {
             const float *gsrc = src == 0 ? lv.in0 : lv.in1;
             float *sdst = src == 0 ? in0 : in1;
 #pragma unroll 1
-            for (int r0 = warp * kStageRows; r0 < nin; r0 += W * kStageRows) {
+            for (int r0 = warp * kStageRows; r0 < nin; r0 += W * kStageRows) {   // one round
                 float buf[kStageRows][CPL];
 #pragma unroll
                 for (int u = 0; u < kStageRows; ++u) {
