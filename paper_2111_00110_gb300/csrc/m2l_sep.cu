@@ -71,7 +71,13 @@ struct SepArgs {
     int goff[(kMaxOrder + 1) * (kMaxOrder + 1)];   // offset of group (i0, i1) in a 4-indexed row
     int nslot;                                     // task slots of the table (pairs plus empty slots)
     char2 pair[kSepMaxSlots];                      // task pair (i, j), i + j <= rho, by slot; (-1, -1): none
+    int ahead;   // finest level: a block prefetches into L2 the input rows of block + ahead (0: none)
 };
+
+// bulk prefetch of `bytes` (a multiple of 16) from a 16-byte aligned global address into L2
+__device__ __forceinline__ void prefetch_l2(const float *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes) : "memory");
+}
 
 // In shared memory rows are padded to an odd number of floats so that the 32 lanes of a warp,
 // which work on 32 consecutive cells, read 32 different banks.
@@ -443,6 +449,22 @@ __global__ void __launch_bounds__(sep_threads(RHO), RHO >= 7 ? 1 : 3) k_m2l_sep(
     constexpr int HALO = FINEST ? 2 : 3;
     const int nin = nt + 2 * HALO;
 
+    // finest level at orders 7-8: the last warp asks L2 for the input rows of the block `ahead`
+    // blocks on (a wave later), so that its staging finds them there (order-8 M2L 2.56 -> 2.40 ms
+    // per step; at order 6, whose warps load all their rows in one round, it cost 2 %)
+    if (FINEST && RHO >= 7 && args.ahead > 0 && threadIdx.x >= kSepThreads - 32) {
+        const int b2 = bl + args.ahead;
+        if (b2 < n * n * lv.nseg) {
+            const int seg2 = b2 % lv.nseg, line2 = b2 / lv.nseg;
+            int64_t base2, stride2;
+            line_geometry<AXIS>(line2, n, base2, stride2);
+            const int t02 = seg2 * lv.seg;
+            const int lo = max(0, t02 - HALO), hi = min(n, t02 + min(lv.seg, n - t02) + HALO);
+            for (int r = lo + (int)(threadIdx.x & 31); r < hi; r += 32)
+                prefetch_l2(lv.in0 + (base2 + (int64_t)r * stride2) * Pt::in, Pt::in * (unsigned)sizeof(float));
+        }
+    }
+
     float *in0 = sm;
     float *in1 = in0 + nin * Pt::sin;
     float *out0 = in1 + (TWO_IN ? nin * Pt::sin : 0);
@@ -765,9 +787,18 @@ static void fill_tables(const fc2t2_plan_s *pl, SepArgs &a, int l_begin, int l_e
 }
 
 template <int RHO, int AXIS, bool FINEST>
-static cudaError_t sep_launch(const SepArgs &a, unsigned blocks, size_t smem, cudaStream_t s) {
+static cudaError_t sep_launch(const SepArgs &a0, unsigned blocks, size_t smem, cudaStream_t s) {
     auto *fn = k_m2l_sep<RHO, AXIS, FINEST>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    SepArgs a = a0;
+    a.ahead = 0;
+    if (FINEST && RHO >= 7) {   // one wave ahead: the blocks resident at once
+        int occ = 0, dev = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, sep_threads(RHO), smem);
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        a.ahead = occ * sms;
+    }
     fn<<<blocks, sep_threads(RHO), smem, s>>>(a);
     return cudaGetLastError();
 }
