@@ -44,7 +44,7 @@ TF32_PER_BF16 = 1.1 / 2.25
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the transform's M2L launches, on
 # the same grid and order at 2^18 points: the M2L launches do not depend on the point count);
 # None where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"separable": 1079081984.0,
+M2L_TRAFFIC_BYTES = {"separable": 1078485760.0,
                      "bf16x3": (464.0 + 82.8) * 1e6}
 
 
