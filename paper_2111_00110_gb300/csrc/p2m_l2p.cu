@@ -306,7 +306,7 @@ __device__ __forceinline__ void l2p_rows(const float4 *rows, int P4, int ra, int
     }
 }
 
-// L2P, staged: a CTA owns SC = min(32, n) consecutive finest cells of one x-line.  Their
+// L2P, staged: a CTA owns SC = min(32 or 64, n) consecutive finest cells of one x-line.  Their
 // coefficient rows are contiguous in memory and are copied to shared memory with coalesced
 // 16-byte loads (all in flight at once); the CTA then walks the cell-sorted points of those cells
 // (a contiguous range of the sort), each thread evaluating its point from the staged row.  So no
@@ -319,7 +319,11 @@ __device__ __forceinline__ void l2p_rows(const float4 *rows, int P4, int ra, int
 //     y(x) = sum_k Lt_0[c_0](k) u_0^k / k!  +  sum_k Lt_1[c_1](k) u_1^k / k!,
 // c_1 = c_0 >> 1 per dimension (the tree's parent rule), u_l = (x - z_l) / h_l.  The SC / 2 parent
 // rows of the segment are contiguous too and are staged beside the finest rows.
-constexpr int kStageCells = 32;
+// cells a CTA stages: 64 with the parent rows (few targets per cell: twice the bytes in flight per
+// CTA) where the rows fit the 48 KB of static shared memory, else 32
+__host__ __device__ constexpr int l2p_stage_cells(int D, int rho, bool two) {
+    return (two && 96 * pad4(ncoef(D, rho)) * 4 <= 48 * 1024) ? 64 : 32;
+}
 
 template <int D, int RHO, bool GRAD, bool TWO>
 __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__restrict__ rec,
@@ -332,6 +336,7 @@ __global__ void __launch_bounds__(kL2PThreads) k_l2p_staged(const float4 *__rest
                                                             float *__restrict__ grad, int accumulate,
                                                             int *__restrict__ err) {
     constexpr int Pp = pad4(ncoef(D, RHO)), P4 = Pp / 4;
+    constexpr int kStageCells = l2p_stage_cells(D, RHO, TWO);
     __shared__ alignas(16) float4 rows[(kStageCells + (TWO ? kStageCells / 2 : 0)) * P4];
     __shared__ uint64_t staged;   // mbarrier: the bulk copies of the rows have landed
     const int sc = n < kStageCells ? n : kStageCells;
@@ -457,7 +462,8 @@ static cudaError_t launch_l2p_staged(const fc2t2_plan_s *pl, cudaStream_t s, con
                                      float *val, float *grad_times_w, bool accumulate) {
     if (m == 0) return cudaSuccess;
     if (TWO && pl->nlev < 2) return cudaErrorInvalidValue;
-    const int sc = pl->n < kStageCells ? pl->n : kStageCells;
+    const int cells = l2p_stage_cells(pl->D, pl->rho, TWO);
+    const int sc = pl->n < cells ? pl->n : cells;
     const unsigned blocks = (unsigned)(pl->lev[0].G / sc);
     const float h0 = (float)pl->lev[0].h, inv_h0 = (float)(1.0 / pl->lev[0].h);
     const float h1 = TWO ? (float)pl->lev[1].h : 1.0f, inv_h1 = TWO ? (float)(1.0 / pl->lev[1].h) : 1.0f;
