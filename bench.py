@@ -704,10 +704,13 @@ def measure_fit(dev, flush, steps, n=1 << 24, adam_steps=100, n_ref=2048, check=
 
 def measure_batched(dev, flush, steps, warmup, n_inst=64):
     """The batched workload: 64 independent clustered point sets (N_i = M_i log-uniform in
-    [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3) and order (4 or 6) chosen by the
-    autotuner (fastest candidate within 1e-2 rel-L2 of the exact sum, separable M2L).  A step is one
-    batched forward and one batched backward call over all instances (a stream per plan, instances
-    side by side); the same instances run one call after another on one stream for comparison."""
+    [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3), order (4, 6 or 8) and M2L form
+    (separable line passes over the whole grid, or the occupied-cell work queue) chosen by the
+    autotuner (fastest candidate within 1e-2 rel-L2 of the exact sum).  A step is one batched
+    forward and one batched backward call over all instances: each instance's sorts, P2M and M2M on
+    its plan's stream, one persistent M2L launch for all occupied-cell instances of an order, then
+    L2L and L2P per instance; the same instances run one call after another on one stream for
+    comparison."""
     import time
     import torch
     from paper_2111_00110_gb300 import autotune, workloads
@@ -717,8 +720,8 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     ws = [torch.from_numpy(wl.w).to(dev) for wl in wls]
     qs = [torch.from_numpy(wl.q).to(dev) for wl in wls]
     t0 = time.time()
-    choices = [autotune.autotune(p, w, q, wl.sigma, target=1e-2, grids=(32, 64), orders=(4, 6),
-                                 m2l=("separable",), sample=512, reps=1)[0]
+    choices = [autotune.autotune(p, w, q, wl.sigma, target=1e-2, grids=(32, 64), orders=(4, 6, 8),
+                                 m2l=("occupied", "separable"), sample=512, reps=1)[0]
                for wl, p, w, q in zip(wls, ps, ws, qs)]
     tune_s = time.time() - t0
     plans = [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, device=dev)
@@ -727,12 +730,12 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
 
     def step_batched():
         ys = forward_batched(plans, ps, ws, qs)
-        backward_batched(plans, ps, ws, qs, ys)
+        backward_batched(plans, ps, ws, qs, ys, reuse_forward=True)
 
     def step_sequential():
         for pl, p, w, q in zip(plans, ps, ws, qs):
             y = pl.forward(p, w, q)
-            pl.backward(p, w, q, y)
+            pl.backward(p, w, q, y, reuse_forward=True)
 
     def timed(fn):
         for _ in range(max(3, warmup)):
@@ -754,7 +757,7 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     queries = sum(wl.M for wl in wls)
     hist = {}
     for c in choices:
-        key = f"{c.grid}^3 order {c.order}"
+        key = f"{c.grid}^3 order {c.order} {c.m2l}"
         hist[key] = hist.get(key, 0) + 1
     for pl in plans:
         pl.close()

@@ -84,9 +84,20 @@ typedef enum {
                                     three products (hi*hi + hi*lo + lo*hi): FP32 accuracy */
     FC2T2_M2L_BF16X3 = 4,        /* as TF32X3 with BF16 parts (~16 significant bits per operand,
                                     half the MMA instructions): within the FP32 error bar */
-    FC2T2_M2L_SEPARABLE = 5      /* FP32 on the CUDA cores, the Gaussian's derivative table
+    FC2T2_M2L_SEPARABLE = 5,     /* FP32 on the CUDA cores, the Gaussian's derivative table
                                     factored per dimension: three one-dimensional passes per
                                     level (same operator and interaction lists, far fewer flops) */
+    FC2T2_M2L_OCCUPIED = 6       /* FP32 on the CUDA cores, the direct operator over occupied
+                                    cells only: a target cell with targets below it takes the
+                                    terms of the source cells of its interaction list that hold
+                                    sources (the others' moments are zero; the other targets'
+                                    series are never read).  The same terms as FP32 for every
+                                    series that is read; the work scales with the occupied cell
+                                    pairs, not the grid (clustered points).  Any kernel, 2D and 3D.
+                                    One persistent launch over a device work queue per call (per
+                                    batched call for the plans of one dimension and order).  The
+                                    local series of cells with no target are left unspecified, so
+                                    fc2t2_expand and the ray calls take every cell as a target. */
 } fc2t2_m2l_prec;
 
 typedef struct fc2t2_plan_s *fc2t2_plan;
@@ -268,9 +279,14 @@ FC2T2_API fc2t2_status fc2t2_ray_backward(fc2t2_plan plan, void *stream, const f
  * plan stream is joined back into `stream` before the call returns, so work enqueued on `stream`
  * afterwards sees all results.  The call is equivalent to n_inst calls of fc2t2_forward /
  * fc2t2_backward and can be captured into a CUDA graph by the caller (with check_domain off: the
- * fork / join become parallel branches).  Errors: INVALID_ARG (n_inst < 0, a NULL array or plan),
- * and any error of the single-instance call, for the first failing instance (the remaining
- * instances are not enqueued; the plan streams are joined all the same). */
+ * fork / join become parallel branches).  Instances whose plan has the OCCUPIED M2L (one channel,
+ * points on both sides, a plan that serves no other instance of the call) share the M2L: each runs
+ * its sorts, P2M, occupancy and M2M on its plan's stream, then one persistent launch on `stream`
+ * takes the occupied cell pairs of all of them (one launch per dimension and order, per 64
+ * instances) from a device work queue, then each runs L2L and L2P on its stream.  Errors:
+ * INVALID_ARG (n_inst < 0, a NULL array or plan), and any error of the single-instance call, for
+ * the first failing instance (the remaining instances are not enqueued; the plan streams are
+ * joined all the same). */
 FC2T2_API fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream,
                                              const float *const *p, const float *const *w, const int64_t *N,
                                              const float *const *q, const int64_t *M, float *const *y);
@@ -278,6 +294,15 @@ FC2T2_API fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plan
                                               const float *const *p, const float *const *w, const int64_t *N,
                                               const float *const *q, const int64_t *M,
                                               const float *const *ybar, float *const *wbar, float *const *pbar);
+/* fc2t2_backward_batched after fc2t2_forward_batched on the same plans and arrays (the batched
+ * form of fc2t2_backward_reuse: an instance whose plan's sorts were made from these pointers and
+ * sizes reuses them, the cotangent gathered into the existing order of q; the caller promises
+ * unchanged contents).  Same results and errors as fc2t2_backward_batched. */
+FC2T2_API fc2t2_status fc2t2_backward_batched_reuse(int n_inst, const fc2t2_plan *plans, void *stream,
+                                                    const float *const *p, const float *const *w, const int64_t *N,
+                                                    const float *const *q, const int64_t *M,
+                                                    const float *const *ybar, float *const *wbar,
+                                                    float *const *pbar);
 
 /* What a plan computes per transform (forward or backward), for performance accounting. */
 typedef struct {

@@ -24,7 +24,7 @@ STATUS = {
     6: "FC2T2_ERR_TIMEOUT",
 }
 KERNELS = {"gaussian": 0, "poly": 1}
-M2L_PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4, "separable": 5}
+M2L_PREC = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4, "separable": 5, "occupied": 6}
 
 # every entry point declared in include/fc2t2.h
 EXPORTS = (
@@ -39,6 +39,7 @@ EXPORTS = (
     "fc2t2_forward_noalloc",
     "fc2t2_forward_batched",
     "fc2t2_backward_batched",
+    "fc2t2_backward_batched_reuse",
     "fc2t2_plan_query",
     "fc2t2_plan_check",
     "fc2t2_direct",
@@ -121,6 +122,7 @@ def load(path: str = LIB_PATH):
         lib.fc2t2_forward_noalloc.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
         lib.fc2t2_forward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fc2t2_backward_batched.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        lib.fc2t2_backward_batched_reuse.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         lib.fc2t2_plan_query.argtypes = [vp, ctypes.POINTER(PlanInfo)]
         lib.fc2t2_plan_check.argtypes = [vp, vp]
         lib.fc2t2_direct.argtypes = [ctypes.POINTER(PlanDesc), vp, vp, vp, i64, vp, i64, vp]
@@ -134,7 +136,7 @@ def load(path: str = LIB_PATH):
         for name in ("fc2t2_plan_create", "fc2t2_plan_destroy", "fc2t2_forward", "fc2t2_backward",
                      "fc2t2_last_error", "fc2t2_profile_enable", "fc2t2_profile_read",
                      "fc2t2_forward_noalloc", "fc2t2_forward_batched", "fc2t2_backward_batched",
-                     "fc2t2_plan_query"):
+                     "fc2t2_backward_batched_reuse", "fc2t2_plan_query"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -249,10 +251,11 @@ def forward_batched(plans, stream, p, w, N, q, M, y) -> None:
     _kept.clear()
 
 
-def backward_batched(plans, stream, p, w, N, q, M, ybar, wbar, pbar) -> None:
+def backward_batched(plans, stream, p, w, N, q, M, ybar, wbar, pbar, reuse: bool = False) -> None:
     n = len(plans)
     i64 = ctypes.c_int64 * n
-    check(load().fc2t2_backward_batched(n, ctypes.addressof(_keep(_ptr_array(plans))), stream,
+    fn = load().fc2t2_backward_batched_reuse if reuse else load().fc2t2_backward_batched
+    check(fn(n, ctypes.addressof(_keep(_ptr_array(plans))), stream,
                                         ctypes.addressof(_keep(_ptr_array(p))), ctypes.addressof(_keep(_ptr_array(w))),
                                         ctypes.addressof(_keep(i64(*N))), ctypes.addressof(_keep(_ptr_array(q))),
                                         ctypes.addressof(_keep(i64(*M))), ctypes.addressof(_keep(_ptr_array(ybar))),

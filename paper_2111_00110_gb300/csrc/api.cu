@@ -1,5 +1,6 @@
 // C ABI of the FC2T2 library: plan creation (operator tables, workspace) and the
 // forward / backward pipelines (Sec. 3 and Sec. 4.1 of arXiv 2111.00110).
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <memory>
@@ -273,9 +274,41 @@ static void destroy(fc2t2_plan_s *pl) {
     cudaFree(pl->d_mma_ops);
     for (int l = 0; l < kMaxLevels; ++l) cudaFree(pl->tc.packed[l]);
     cudaFree(pl->sep.d_t);
+    cudaFree(pl->occ.act); cudaFree(pl->occ.list); cudaFree(pl->occ.cnt); cudaFree(pl->occ.chunk_off);
+    cudaFree(pl->occ.next); cudaFree(pl->occ.d_inst);
     free_sort(pl->src);
     free_sort(pl->qry);
     delete pl;
+}
+
+// M2L over occupied cells: occupancy bytes, target lists, the work queue, and the plan's
+// descriptor for the queue's kernel (device memory, written once)
+static fc2t2_status build_occ(fc2t2_plan_s *pl) {
+    auto &o = pl->occ;
+    fc2t2_status st;
+    if ((st = dev_alloc(&o.act, (size_t)pl->G_total, "occupancy")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&o.list, (size_t)pl->G_total, "occupied targets")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&o.cnt, (size_t)kOccBuckets, "occupied target counts")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&o.chunk_off, (size_t)kOccMaxInst * kOccBuckets + 1, "work queue")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&o.next, (size_t)1, "work counter")) != FC2T2_OK) return st;
+    if ((st = dev_alloc(&o.d_inst, (size_t)1, "queue descriptor")) != FC2T2_OK) return st;
+    OccInst h{};
+    h.M = pl->d_M;
+    h.L = pl->d_L;
+    h.dtab = pl->d_dtab;
+    h.act = o.act;
+    h.list = o.list;
+    h.cnt = o.cnt;
+    h.nlev = pl->nlev;
+    h.n0 = pl->n;
+    for (int l = 0; l < pl->nlev; ++l) h.off[l] = pl->lev[l].off;
+    if ((st = check_cuda(cudaMemcpy(o.d_inst, &h, sizeof(h), cudaMemcpyHostToDevice), "upload queue descriptor")) != FC2T2_OK)
+        return st;
+    // the series of cells without targets are never read; zero them once so that they are finite
+    if ((st = check_cuda(cudaMemset(pl->d_L, 0, sizeof(float) * (size_t)pl->G_total * pl->Pp), "clear locals")) != FC2T2_OK)
+        return st;
+    o.enabled = 1;
+    return FC2T2_OK;
 }
 
 static fc2t2_status build_tables(fc2t2_plan_s *pl) {
@@ -308,6 +341,7 @@ static fc2t2_status build_tables(fc2t2_plan_s *pl) {
     if ((st = upload(pl->d_dtab, dtab, "upload derivative tables")) != FC2T2_OK) return st;
     // tensor-core operator images (3D; other dimensions keep the CUDA-core M2L)
     if (pl->desc.m2l == FC2T2_M2L_SEPARABLE) return build_sep(pl, dtab64);
+    if (pl->desc.m2l == FC2T2_M2L_OCCUPIED) return build_occ(pl);
     if (pl->desc.m2l != FC2T2_M2L_FP32 && D == 3)
         if ((st = build_tc_operators(pl, dtab64)) != FC2T2_OK) return st;
     return FC2T2_OK;
@@ -337,7 +371,8 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     }
     if (d->channels < 1 || d->channels > 4096) return set_error(FC2T2_ERR_INVALID_ARG, "channels must be in [1, 4096]");
     if (d->m2l != FC2T2_M2L_FP32 && d->m2l != FC2T2_M2L_TF32 && d->m2l != FC2T2_M2L_BF16 &&
-        d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3 && d->m2l != FC2T2_M2L_SEPARABLE)
+        d->m2l != FC2T2_M2L_TF32X3 && d->m2l != FC2T2_M2L_BF16X3 && d->m2l != FC2T2_M2L_SEPARABLE &&
+        d->m2l != FC2T2_M2L_OCCUPIED)
         return set_error(FC2T2_ERR_UNSUPPORTED, "unknown M2L precision");
     if (d->m2l == FC2T2_M2L_SEPARABLE && (d->kernel != FC2T2_KERNEL_GAUSSIAN || d->dim != 3))
         return set_error(FC2T2_ERR_UNSUPPORTED, "the separable M2L needs the Gaussian kernel and dim = 3");
@@ -480,11 +515,18 @@ static fc2t2_status evaluate_targets(fc2t2_plan_s *pl, cudaStream_t s, const Sor
 // P2M .. M2L .. L2L: expansion of sorted sources into local coefficients: with l2l, the finest
 // level's rows of d_L hold the whole local series; without, L2L stops at level 1 and the finest
 // level's rows hold its own M2L only (for launch_l2p_two)
-static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork *src, bool l2l = true) {
+static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork *src, const SortWork *tgt,
+                           bool l2l = true) {
     fc2t2_status st;
     if (src) {   // (NULL: the finest moments are already in place, e.g. from ray2M)
         StageScope scope(pl, s, FC2T2_STAGE_P2M);
         if ((st = check_cuda(launch_p2m(pl, s, *src, pl->d_M), "p2m")) != FC2T2_OK) return st;
+    }
+    if (pl->occ.enabled) {   // which cells hold sources / have targets below them (NULL: all)
+        StageScope scope(pl, s, FC2T2_STAGE_M2L);
+        if ((st = check_cuda(launch_occupancy(pl, s, src ? src->count : nullptr, tgt ? tgt->count : nullptr),
+                             "occupancy")) != FC2T2_OK)
+            return st;
     }
     if (forks(pl)) {
         // The finest level's M2L needs only the finest moments; everything above it (M2M, the
@@ -520,6 +562,9 @@ static fc2t2_status expand(fc2t2_plan_s *pl, cudaStream_t s, const SortWork *src
         StageScope scope(pl, s, FC2T2_STAGE_M2L);
         if (pl->sep.enabled) {
             if ((st = check_cuda(launch_m2l_sep(pl, s), "m2l (separable)")) != FC2T2_OK) return st;
+        } else if (pl->occ.enabled) {
+            const fc2t2_plan_s *one = pl;
+            if ((st = check_cuda(launch_m2l_occ(&one, 1, s), "m2l (occupied cells)")) != FC2T2_OK) return st;
         } else {
             if (pl->tc.enabled && (st = check_cuda(launch_m2l_tc_all(pl, s), "m2l (tensor cores)")) != FC2T2_OK)
                 return st;
@@ -649,7 +694,7 @@ fc2t2_status fc2t2_forward(fc2t2_plan pl, void *stream, const float *p, const fl
     const bool two = l2p_two_levels(pl, M);
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, &pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, &pl->qry, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, y + (int64_t)c * M, nullptr, false)) != FC2T2_OK)
             return st;
@@ -684,7 +729,7 @@ fc2t2_status fc2t2_backward(fc2t2_plan pl, void *stream, const float *p, const f
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
             if (pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, &pl->qry, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->qry, &pl->src, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         // pbar sums the channels' contributions w[c] * grad g_c
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
@@ -713,7 +758,7 @@ fc2t2_status fc2t2_backward_reuse(fc2t2_plan pl, void *stream, const float *p, c
         if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         // (one channel: the sort of p still carries w)
         if (C > 1 && pbar && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, &pl->qry, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->qry, &pl->src, !two)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
             FC2T2_OK)
             return st;
@@ -747,7 +792,7 @@ fc2t2_status fc2t2_backward_q(fc2t2_plan pl, void *stream, const float *p, const
             if ((st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
             if ((st = reweight(pl, s, ybar + (int64_t)c * M, M, pl->qry)) != FC2T2_OK) return st;
         }
-        if ((st = expand(pl, s, &pl->src, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, &pl->qry, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->qry, M, two, nullptr, qbar, c > 0)) != FC2T2_OK) return st;
     }
@@ -771,7 +816,7 @@ fc2t2_status fc2t2_ray_forward(fc2t2_plan pl, void *stream, const float *p, cons
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, &pl->src, true)) != FC2T2_OK) return st;   // the finest series, complete
+        if ((st = expand(pl, s, &pl->src, nullptr, true)) != FC2T2_OK) return st;   // the finest series, complete
         StageScope scope(pl, s, FC2T2_STAGE_L2P);
         if ((st = check_cuda(launch_ray_forward(pl, s, rays, R, y + (int64_t)c * R), "ray integrals")) != FC2T2_OK)
             return st;
@@ -803,7 +848,7 @@ fc2t2_status fc2t2_ray_backward(fc2t2_plan pl, void *stream, const float *p, con
             if ((st = check_cuda(launch_ray2m(pl, s, rays, R, ybar + (int64_t)c * R, pl->d_M), "ray2M")) != FC2T2_OK)
                 return st;
         }
-        if ((st = expand(pl, s, nullptr, !two)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, nullptr, &pl->src, !two)) != FC2T2_OK) return st;
         if (c == 0 && (st = wait_targets(pl, s)) != FC2T2_OK) return st;
         if ((st = evaluate_targets(pl, s, pl->src, N, two, wbar ? wbar + (int64_t)c * N : nullptr, pbar, c > 0)) !=
             FC2T2_OK)
@@ -832,7 +877,7 @@ fc2t2_status fc2t2_expand(fc2t2_plan pl, void *stream, const float *p, const flo
     if ((st = sort_points(pl, s, p, w, N, pl->src)) != FC2T2_OK) return st;
     for (int c = 0; c < C; ++c) {
         if (c > 0 && (st = reweight(pl, s, w + (int64_t)c * N, N, pl->src)) != FC2T2_OK) return st;
-        if ((st = expand(pl, s, &pl->src)) != FC2T2_OK) return st;
+        if ((st = expand(pl, s, &pl->src, nullptr)) != FC2T2_OK) return st;
         // (one channel: the finest level of d_L is the held expansion)
         if (C > 1 && (st = check_cuda(cudaMemcpyAsync(hold + (size_t)c * row_floats, pl->d_L, sizeof(float) * row_floats,
                                                       cudaMemcpyDeviceToDevice, s),
@@ -953,6 +998,73 @@ fc2t2_status batch_join(int n_inst, const fc2t2_plan *plans, cudaStream_t s, uin
 
 }  // namespace
 
+// Instances of a batched call whose M2L joins the batch's shared launch: occupied-cell plans with
+// one channel and points on both sides (the others run their whole transform on their stream).
+static bool occ_batched(const fc2t2_plan_s *pl, int64_t n_src, int64_t n_tgt) {
+    return pl->occ.enabled && pl->C == 1 && n_src > 0 && n_tgt > 0 && !pl->profiling;
+}
+
+// Whether the plan of instance i serves another instance of the batch too: its instances then run
+// one after another on the plan's stream (one workspace), none of them in the shared M2L launch.
+static bool plan_repeats(int n_inst, const fc2t2_plan *plans, int i) {
+    for (int k = 0; k < n_inst; ++k)
+        if (k != i && plans[k] == plans[i]) return true;
+    return false;
+}
+
+// One instance of a batched transform up to its M2L: sorts of targets (tx, tw) and sources
+// (sx, sw), P2M, occupancy, M2M.  `tgt` / `srt` are the plan's sort workspaces for them.
+static fc2t2_status occ_prepare(fc2t2_plan_s *pl, cudaStream_t s, const float *sx, const float *sw, int64_t ns,
+                                SortWork &srt, const float *tx, const float *tw, int64_t nt, SortWork &tgt,
+                                bool sorted = false) {
+    if (ns > srt.cap || nt > tgt.cap) return set_error(FC2T2_ERR_INVALID_ARG, "N or M outside [0, max]");
+    fc2t2_status st;
+    if ((st = clear_flags(pl, s)) != FC2T2_OK) return st;
+    if (sorted) {   // both sorts hold these points: only the source weights change
+        if ((st = reweight(pl, s, sw, ns, srt)) != FC2T2_OK) return st;
+    } else {
+        if ((st = sort_points(pl, s, tx, tw, nt, tgt)) != FC2T2_OK) return st;
+        if ((st = sort_points(pl, s, sx, sw, ns, srt)) != FC2T2_OK) return st;
+    }
+    if ((st = check_cuda(launch_p2m(pl, s, srt, pl->d_M), "p2m")) != FC2T2_OK) return st;
+    if ((st = check_cuda(launch_occupancy(pl, s, srt.count, tgt.count), "occupancy")) != FC2T2_OK) return st;
+    for (int l = 0; l + 1 < pl->nlev; ++l)
+        if ((st = check_cuda(launch_m2m(pl, s, l), "m2m")) != FC2T2_OK) return st;
+    return FC2T2_OK;
+}
+
+// After the batch's M2L: L2L and L2P of one instance (value into val, gradient times weight into grad)
+static fc2t2_status occ_finish(fc2t2_plan_s *pl, cudaStream_t s, const SortWork &tgt, int64_t nt, float *val,
+                               float *grad) {
+    const bool two = l2p_two_levels(pl, nt);
+    fc2t2_status st;
+    for (int l = pl->nlev - 2; l >= (two ? 1 : 0); --l)
+        if ((st = check_cuda(launch_l2l(pl, s, l), "l2l")) != FC2T2_OK) return st;
+    if ((st = evaluate_targets(pl, s, tgt, nt, two, val, grad, false)) != FC2T2_OK) return st;
+    return finish_flags(pl, s);
+}
+
+// The M2L of every batched occupied-cell instance: one persistent launch per (dimension, order)
+// and per kOccMaxInst instances, on the call's stream.
+static fc2t2_status occ_batch_m2l(int n_inst, const fc2t2_plan *plans, const std::vector<char> &joins, cudaStream_t s) {
+    std::vector<const fc2t2_plan_s *> todo;
+    for (int i = 0; i < n_inst; ++i)
+        if (joins[i]) todo.push_back(plans[i]);
+    while (!todo.empty()) {
+        std::vector<const fc2t2_plan_s *> group, rest;
+        for (auto *pl : todo)
+            if (pl->D == todo[0]->D && pl->rho == todo[0]->rho && (int)group.size() < kOccMaxInst &&
+                std::find(group.begin(), group.end(), pl) == group.end())
+                group.push_back(pl);
+            else
+                rest.push_back(pl);
+        fc2t2_status st = check_cuda(launch_m2l_occ(group.data(), (int)group.size(), s), "m2l (occupied cells, batched)");
+        if (st != FC2T2_OK) return st;
+        todo.swap(rest);
+    }
+    return FC2T2_OK;
+}
+
 fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
                                    float *const *y) {
@@ -962,17 +1074,43 @@ fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *st
     for (int i = 0; i < n_inst; ++i)
         if (!plans[i]) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    const uint64_t mark = ++g_batch_counter;
+    // occupied-cell instances: sorts .. M2M on their streams, one M2L launch for all, then L2L, L2P
+    std::vector<char> joins(n_inst, 0);
+    bool any = false;
+    for (int i = 0; i < n_inst; ++i) {
+        if (!occ_batched(plans[i], N[i], M[i]) || plan_repeats(n_inst, plans, i)) continue;
+        if (!p[i] || !w[i] || !q[i] || !y[i]) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+        joins[i] = 1;
+        any = true;
+    }
+    uint64_t mark = ++g_batch_counter;
     fc2t2_status st = batch_fork(n_inst, plans, s, mark);
+    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i) {
+        fc2t2_plan_s *pl = plans[i];
+        st = joins[i] ? occ_prepare(pl, pl->run, p[i], w[i], N[i], pl->src, q[i], nullptr, M[i], pl->qry)
+                      : fc2t2_forward(pl, pl->run, p[i], w[i], N[i], q[i], M[i], y[i]);
+    }
+    fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+    if (st != FC2T2_OK || sj != FC2T2_OK || !any) return st != FC2T2_OK ? st : sj;
+    if ((st = occ_batch_m2l(n_inst, plans, joins, s)) != FC2T2_OK) return st;
+    mark = ++g_batch_counter;
+    std::vector<fc2t2_plan> sub;
+    for (int i = 0; i < n_inst; ++i)
+        if (joins[i]) sub.push_back(plans[i]);
+    st = batch_fork((int)sub.size(), sub.data(), s, mark);
     for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
-        st = fc2t2_forward(plans[i], plans[i]->run, p[i], w[i], N[i], q[i], M[i], y[i]);
-    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+        if (joins[i]) {
+            fc2t2_plan_s *pl = plans[i];
+            st = occ_finish(pl, pl->run, pl->qry, M[i], y[i], nullptr);
+            pl->src.held_w = w[i];
+        }
+    sj = batch_join((int)sub.size(), sub.data(), s, mark);
     return st != FC2T2_OK ? st : sj;
 }
 
-fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
-                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
-                                    const float *const *ybar, float *const *wbar, float *const *pbar) {
+static fc2t2_status backward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
+                                     const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
+                                     const float *const *ybar, float *const *wbar, float *const *pbar, bool reuse) {
     if (n_inst < 0) return set_error(FC2T2_ERR_INVALID_ARG, "n_inst < 0");
     if (n_inst == 0) return FC2T2_OK;
     if (!plans || !p || !w || !N || !q || !M || !ybar || !wbar || !pbar)
@@ -980,12 +1118,58 @@ fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *s
     for (int i = 0; i < n_inst; ++i)
         if (!plans[i]) return set_error(FC2T2_ERR_INVALID_ARG, "plan is NULL");
     cudaStream_t s = (cudaStream_t)stream;
-    const uint64_t mark = ++g_batch_counter;
+    // occupied-cell instances (the transposed transform: sources q with weights ybar, targets p):
+    // sorts .. M2M on their streams, one M2L launch for all, then L2L, L2P value and gradient
+    std::vector<char> joins(n_inst, 0);
+    bool any = false;
+    for (int i = 0; i < n_inst; ++i) {
+        if (!occ_batched(plans[i], M[i], N[i]) || (!wbar[i] && !pbar[i]) || plan_repeats(n_inst, plans, i)) continue;
+        if (!p[i] || !w[i] || !q[i] || !ybar[i]) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
+        joins[i] = 1;
+        any = true;
+    }
+    uint64_t mark = ++g_batch_counter;
     fc2t2_status st = batch_fork(n_inst, plans, s, mark);
+    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i) {
+        fc2t2_plan_s *pl = plans[i];
+        // (reuse: the forward's sorts of exactly these arrays, as fc2t2_backward_reuse checks)
+        const bool sorted = reuse && pl->src.held_x == p[i] && pl->src.held_w == w[i] && pl->src.held_n == N[i] &&
+                            pl->qry.held_x == q[i] && pl->qry.held_n == M[i];
+        if (joins[i])
+            st = occ_prepare(pl, pl->run, q[i], ybar[i], M[i], pl->qry, p[i], w[i], N[i], pl->src, sorted);
+        else if (reuse)
+            st = fc2t2_backward_reuse(pl, pl->run, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
+        else
+            st = fc2t2_backward(pl, pl->run, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
+    }
+    fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+    if (st != FC2T2_OK || sj != FC2T2_OK || !any) return st != FC2T2_OK ? st : sj;
+    if ((st = occ_batch_m2l(n_inst, plans, joins, s)) != FC2T2_OK) return st;
+    mark = ++g_batch_counter;
+    std::vector<fc2t2_plan> sub;
+    for (int i = 0; i < n_inst; ++i)
+        if (joins[i]) sub.push_back(plans[i]);
+    st = batch_fork((int)sub.size(), sub.data(), s, mark);
     for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
-        st = fc2t2_backward(plans[i], plans[i]->run, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
-    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+        if (joins[i]) {
+            fc2t2_plan_s *pl = plans[i];
+            st = occ_finish(pl, pl->run, pl->src, N[i], wbar[i], pbar[i]);
+        }
+    sj = batch_join((int)sub.size(), sub.data(), s, mark);
     return st != FC2T2_OK ? st : sj;
+}
+
+fc2t2_status fc2t2_backward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
+                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
+                                    const float *const *ybar, float *const *wbar, float *const *pbar) {
+    return backward_batched(n_inst, plans, stream, p, w, N, q, M, ybar, wbar, pbar, false);
+}
+
+fc2t2_status fc2t2_backward_batched_reuse(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
+                                          const float *const *w, const int64_t *N, const float *const *q,
+                                          const int64_t *M, const float *const *ybar, float *const *wbar,
+                                          float *const *pbar) {
+    return backward_batched(n_inst, plans, stream, p, w, N, q, M, ybar, wbar, pbar, true);
 }
 
 fc2t2_status fc2t2_plan_query(fc2t2_plan pl, fc2t2_plan_info *info) {

@@ -214,6 +214,28 @@ struct Level {
     double h;           // cell width
 };
 
+// M2L over occupied cells: one plan's arrays as the work queue's kernel reads them (kept in device
+// memory, written once at plan creation), and the queue of one launch over one or more plans.
+constexpr int kOccBuckets = kMaxLevels * 8;    // (level, parity class) buckets per plan
+constexpr int kOccMaxInst = 64;                // plans per launch
+struct OccInst {
+    const float *M;              // moments of every level [G_total][Pp]
+    float *L;                    // locals of every level
+    const float *dtab;           // [nlev][7^D][Pp] scaled kernel derivatives
+    const unsigned char *act;    // [G_total] bit 0: sources below the cell, bit 1: targets below it
+    const int *list;             // [G_total] occupied targets: bucket (l, cls) at off[l] + cls * G_l / 2^D
+    const int *cnt;              // [kOccBuckets] bucket sizes, (l, cls) at 8 l + cls
+    int nlev, n0;                // levels, finest cells per dimension
+    int64_t off[kMaxLevels];     // first cell of each level
+};
+struct OccQueue {
+    const OccInst *inst[kOccMaxInst];
+    int ninst;
+    int chunk;                   // targets per work item (a chunk of one bucket)
+    int *chunk_off;              // [ninst * kOccBuckets + 1] first chunk of every bucket, then the total
+    int *next;                   // the next chunk to take
+};
+
 }  // namespace fc2t2
 
 struct fc2t2_plan_s {
@@ -275,6 +297,16 @@ struct fc2t2_plan_s {
         double flops = 0.0;
     } sep;
 
+    struct OccInfo {             // M2L over occupied cells
+        int enabled = 0;
+        unsigned char *act = nullptr;   // [G_total] occupancy bytes
+        int *list = nullptr;            // [G_total] occupied targets by (level, class)
+        int *cnt = nullptr;             // [kOccBuckets]
+        int *chunk_off = nullptr;       // [kOccMaxInst * kOccBuckets + 1] (a batched launch uses its first plan's)
+        int *next = nullptr;            // [1]
+        fc2t2::OccInst *d_inst = nullptr;
+    } occ;
+
     // diagnostics: kernel launches per stage, and (when enabled) event pairs per stage
     mutable int64_t launches[FC2T2_NUM_STAGES] = {};
     bool profiling = false;
@@ -325,6 +357,12 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64);
 // part 0: every level; 1: the finest level; 2: the levels above it
 cudaError_t launch_m2l_sep(const fc2t2_plan_s *pl, cudaStream_t s, int part = 0);
 cudaError_t launch_m2l_tc_all(const fc2t2_plan_s *pl, cudaStream_t s);
+// occupancy of every level from the finest cells' counts of the sources and targets (NULL: every
+// cell occupied), and the occupied targets' lists
+cudaError_t launch_occupancy(const fc2t2_plan_s *pl, cudaStream_t s, const int *src_cnt, const int *tgt_cnt);
+// M2L over occupied cells of every level of `nplan` plans of one dimension and order, one
+// persistent launch (after launch_occupancy and M2M of each)
+cudaError_t launch_m2l_occ(const fc2t2_plan_s *const *plans, int nplan, cudaStream_t s);
 // register-resident M2M / L2L for orders <= 6 (return false when not applicable)
 bool launch_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);
 bool launch_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level, cudaError_t &err);

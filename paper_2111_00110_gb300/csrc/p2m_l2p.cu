@@ -103,7 +103,8 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
                                                      const int *__restrict__ start, int n,
                                                      int64_t G, float lo, float h, float inv_h,
                                                      float *__restrict__ M, int *__restrict__ err,
-                                                     int2 *__restrict__ over, unsigned long long *over_ctr) {
+                                                     int2 *__restrict__ over, unsigned long long *over_ctr,
+                                                     int skip_empty) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     extern __shared__ float4 smem4[];   // the block's sorted records, then its output rows
     __shared__ uint64_t staged;
@@ -115,6 +116,9 @@ __global__ void __launch_bounds__(kP2MThreads) k_p2m(const float4 *__restrict__ 
     // past the staged ones, or all of them if the bounded wait gives up, are read from memory.
     const int64_t c_end = (G - c0) < kP2MThreads ? G : c0 + kP2MThreads;
     const int jb0 = __ldg(start + c0), jb1 = __ldg(start + c_end);
+    // (M2L over occupied cells: the rows of cells without sources are never read, so a block whose
+    // cells hold no point leaves them as they are)
+    if (skip_empty && jb1 == jb0) return;
     const int nst = min(jb1 - jb0, kP2MThreads * Pp / 4);
     if (nst > 0) {
         if (threadIdx.x == 0) tc::mbar_init(&staged, 1);
@@ -240,7 +244,7 @@ cudaError_t launch_p2m(const fc2t2_plan_s *pl, cudaStream_t s, const SortWork &w
     FC2T2_DISPATCH(pl->D, pl->rho,
                    (k_p2m<D_, R_><<<blocks, kP2MThreads, smem, s>>>(w.rec, w.start, pl->n, G, pl->lo_f, h, inv_h,
                                                                     M0, pl->d_flags + 2, pl->d_over,
-                                                                    pl->d_over_ctr),
+                                                                    pl->d_over_ctr, pl->occ.enabled),
                     err = cudaGetLastError(),
                     err = err != cudaSuccess ? err
                                              : (k_p2m_over<D_, R_><<<oblocks, 128, 0, s>>>(w.rec, w.start, pl->n,

@@ -11,6 +11,11 @@
 // levels, summing by warp shuffles) shift the child rows and scale the sum by 2^-|a|.  L2L: a
 // child thread loads its parent row, scales by 2^-|g|, shifts it and adds it to its own row.
 // Rows move as 16-byte loads.
+//
+// With the M2L over occupied cells (`act`, the plan's occupancy bytes; NULL otherwise), rows that
+// nothing reads are skipped: the moments of a parent without sources below it are not formed and
+// a child without sources adds nothing (its row may be stale), and the locals of a child without
+// targets below it are not formed.
 #include "dispatch.cuh"
 #include "fc2t2_internal.cuh"
 
@@ -98,10 +103,12 @@ __host__ __device__ constexpr int coef_degree(int D, int k) {
 // M2M at large levels: one thread per parent cell, its children loaded and shifted in turn.
 template <int D, int RHO>
 __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, float *__restrict__ Mp, int np,
-                                                 int64_t Gp) {
+                                                 int64_t Gp, const unsigned char *__restrict__ act_c,
+                                                 const unsigned char *__restrict__ act_p) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     const int64_t C = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (C >= Gp) return;
+    if (act_p && !(act_p[C] & 1)) return;
     int cp[3] = {0, 0, 0};
     {
         int64_t r = C;
@@ -114,6 +121,7 @@ __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, f
     for (int ch = 0; ch < (1 << D); ++ch) {
         int64_t lin = 0;
         for (int d = D - 1; d >= 0; --d) lin = lin * nl + (2 * cp[d] + ((ch >> d) & 1));
+        if (act_c && !(act_c[lin] & 1)) continue;
         float a[P];
         load_row<D, RHO>(Mc + lin * Pp, a);
 #pragma unroll
@@ -133,20 +141,24 @@ __global__ void __launch_bounds__(128) k_m2m_reg(const float *__restrict__ Mc, f
 // (butterfly shuffles), scaled by 2^-|a|; lane ch then writes the coefficients k = ch mod 2^D.
 template <int D, int RHO>
 __global__ void __launch_bounds__(256) k_m2m_child(const float *__restrict__ Mc, float *__restrict__ Mp, int np,
-                                                 int64_t Gp) {
+                                                 int64_t Gp, const unsigned char *__restrict__ act_c,
+                                                 const unsigned char *__restrict__ act_p) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P), NCH = 1 << D;
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t C = t >> D;
     const int ch = (int)(t & (NCH - 1));
     const bool valid = C < Gp;
-    float a[P];
+    int64_t lin = 0;
     if (valid) {
         int cp[3] = {0, 0, 0};
         int64_t r = C;
         for (int d = 0; d < D; ++d) { cp[d] = (int)(r % np); r /= np; }
         const int nl = 2 * np;
-        int64_t lin = 0;
         for (int d = D - 1; d >= 0; --d) lin = lin * nl + (2 * cp[d] + ((ch >> d) & 1));
+    }
+    const bool live = valid && (!act_c || (act_c[lin] & 1));   // (a child without sources adds zero)
+    float a[P];
+    if (live) {
         load_row<D, RHO>(Mc + lin * Pp, a);
 #pragma unroll
         for (int d = 0; d < D; ++d) shift_axis<D, RHO, true>(a, d, ((ch >> d) & 1) ? 0.5f : -0.5f);
@@ -159,7 +171,7 @@ __global__ void __launch_bounds__(256) k_m2m_child(const float *__restrict__ Mc,
     for (int k = 0; k < P; ++k)
 #pragma unroll
         for (int off = 1; off < NCH; off <<= 1) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
-    if (!valid) return;
+    if (!valid || (act_p && !(act_p[C] & 1))) return;
     float *dst = Mp + C * Pp;
 #pragma unroll
     for (int k = 0; k < P; ++k)
@@ -171,10 +183,11 @@ __global__ void __launch_bounds__(256) k_m2m_child(const float *__restrict__ Mc,
 
 template <int D, int RHO>
 __global__ void __launch_bounds__(128) k_l2l_reg(const float *__restrict__ Lp, float *__restrict__ Lc, int nl,
-                                                 int64_t Gc) {
+                                                 int64_t Gc, const unsigned char *__restrict__ act_c) {
     constexpr int P = ncoef(D, RHO), Pp = pad4(P);
     const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= Gc) return;
+    if (act_c && !(act_c[c] & 2)) return;
     int cc[3] = {0, 0, 0};
     {
         int64_t r = c;
@@ -224,18 +237,21 @@ template <int D, int RHO>
 cudaError_t run_m2m_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     {
         const Level &c = pl->lev[level], &p = pl->lev[level + 1];
+        const unsigned char *act = pl->occ.enabled ? pl->occ.act : nullptr;
         // the per-parent form holds two rows in registers: orders <= 6 only
         bool done = false;
         if constexpr (RHO <= 6) {
             if (p.G > 4096) {
                 const unsigned blocks = (unsigned)((p.G + 127) / 128);
-                k_m2m_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G);
+                k_m2m_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G,
+                                                         act ? act + c.off : nullptr, act ? act + p.off : nullptr);
                 done = true;
             }
         }
         if (!done) {
             const unsigned blocks = (unsigned)((p.G * (1 << D) + 255) / 256);
-            k_m2m_child<D, RHO><<<blocks, 256, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G);
+            k_m2m_child<D, RHO><<<blocks, 256, 0, s>>>(pl->d_M + c.off * pl->Pp, pl->d_M + p.off * pl->Pp, p.n, p.G,
+                                                       act ? act + c.off : nullptr, act ? act + p.off : nullptr);
         }
     }
     return cudaGetLastError();
@@ -246,7 +262,8 @@ cudaError_t run_l2l_reg(const fc2t2_plan_s *pl, cudaStream_t s, int level) {
     {
         const Level &p = pl->lev[level + 1], &c = pl->lev[level];
         const unsigned blocks = (unsigned)((c.G + 127) / 128);
-        k_l2l_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_L + p.off * pl->Pp, pl->d_L + c.off * pl->Pp, c.n, c.G);
+        k_l2l_reg<D, RHO><<<blocks, 128, 0, s>>>(pl->d_L + p.off * pl->Pp, pl->d_L + c.off * pl->Pp, c.n, c.G,
+                                                 pl->occ.enabled ? pl->occ.act + c.off : nullptr);
     }
     return cudaGetLastError();
 }

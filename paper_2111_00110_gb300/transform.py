@@ -45,7 +45,8 @@ def resolve_m2l(m2l: str, dim: int, kernel: str, fit: bool) -> str:
 
 class Plan:
     """A transform plan: dimension, finest grid, order, kernel, domain, workspace bounds, M2L form
-    ("auto", "separable", "fp32", "tf32", "bf16", "tf32x3", "bf16x3")."""
+    ("auto", "separable", "occupied", "fp32", "tf32", "bf16", "tf32x3", "bf16x3"); "occupied" runs the
+    direct FP32 operator over the occupied cells only (clustered points)."""
 
     def __init__(self, dim: int, grid: int, order: int, sigma: float = 0.05, *,
                  kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
@@ -291,8 +292,11 @@ def forward_batched(plans: Sequence[Plan], ps, ws, qs):
     return ys
 
 
-def backward_batched(plans: Sequence[Plan], ps, ws, qs, ybars):
-    """(wbar_i, pbar_i) of independent instances through one ``fc2t2_backward_batched`` call."""
+def backward_batched(plans: Sequence[Plan], ps, ws, qs, ybars, reuse_forward: bool = False):
+    """(wbar_i, pbar_i) of independent instances through one ``fc2t2_backward_batched`` call.
+
+    ``reuse_forward``: the tensors are those of the plans' last ``forward_batched`` call and
+    unchanged since, so that call's sorts are reused (``fc2t2_backward_batched_reuse``)."""
     n = len(plans)
     if not (len(ps) == len(ws) == len(qs) == len(ybars) == n):
         raise ValueError("plans, ps, ws, qs and ybars must have the same length")
@@ -308,5 +312,6 @@ def backward_batched(plans: Sequence[Plan], ps, ws, qs, ybars):
     stream = torch.cuda.current_stream(plans[0].device).cuda_stream if n else 0
     capi.backward_batched([pl._h for pl in plans], stream, [_ptr(p) for p in ps], [_ptr(w) for w in ws],
                           [p.shape[0] for p in ps], [_ptr(q) for q in qs], [q.shape[0] for q in qs],
-                          [_ptr(y) for y in ybars], [_ptr(t) for t in wbars], [_ptr(t) for t in pbars])
+                          [_ptr(y) for y in ybars], [_ptr(t) for t in wbars], [_ptr(t) for t in pbars],
+                          reuse=reuse_forward)
     return list(zip(wbars, pbars))

@@ -99,3 +99,11 @@ def test_fitted_operators_exclude_the_separable_m2l(lib):
     out = ctypes.c_void_p(123)
     assert lib.fc2t2_plan_create(ctypes.byref(_desc(m2l=5, fit=1)), ctypes.byref(out)) == 2
     assert out.value is None
+
+
+def test_m2l_form_names_match_the_header():
+    """The binding's M2L form names map to the header's enum values (OCCUPIED included)."""
+    text = open(HEADER).read()
+    vals = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"FC2T2_M2L_(\w+)\s*=\s*(\d+)", text)}
+    assert vals == capi.M2L_PREC
+    assert vals["occupied"] == 6

@@ -255,16 +255,26 @@ def test_direct_sum_matches_the_oracle(lib):
 
 
 def test_autotune_meets_the_target_on_a_batch_instance(lib):
-    """Grid and order chosen per instance: the choice meets the error target against the exact
-    sum and is the fastest candidate that does."""
+    """Grid, order and M2L form chosen per instance: the choice meets the error target against the
+    exact sum and is the fastest candidate that does; a second FP32 form of a (grid, order) whose
+    first one missed the target is not run (same operator, same error)."""
     from paper_2111_00110_gb300.autotune import autotune
     wl = workloads.mixture(3, n_override=30000)
     choice, cands = autotune(dev(wl.p), dev(wl.w), dev(wl.q), 0.02, target=1e-2, grids=(32, 64),
-                             orders=(4, 6, 8), sample=512)
-    print([(c.grid, c.order, round(c.ms, 3), f"{c.err:.2e}") for c in cands], "->", (choice.grid, choice.order))
-    assert len(cands) == 6
+                             orders=(4, 6, 8), m2l=("separable", "occupied"), sample=512)
+    print([(c.grid, c.order, c.m2l, round(c.ms, 3), f"{c.err:.2e}") for c in cands], "->",
+          (choice.grid, choice.order, choice.m2l))
     assert choice.err <= 1e-2
     assert choice.ms == min(c.ms for c in cands if c.err <= 1e-2)
+    by = {}
+    for c in cands:
+        by.setdefault((c.grid, c.order), []).append(c)
+    assert sorted(by) == [(g, o) for g in (32, 64) for o in (4, 6, 8)]
+    for cs in by.values():
+        assert cs[0].m2l == "separable"
+        assert len(cs) == (1 if cs[0].err > 1e-2 else 2)
+        if len(cs) == 2:   # the two FP32 forms of one operator agree to rounding
+            assert abs(cs[0].err - cs[1].err) <= 1e-4 * cs[0].err
     # the error falls with the order on the finer grid (truncation, Sec. 3)
     errs = {(c.grid, c.order): c.err for c in cands}
     assert errs[(64, 8)] < errs[(64, 4)]
