@@ -6,6 +6,7 @@
 #include <memory>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -1065,6 +1066,25 @@ static fc2t2_status occ_batch_m2l(int n_inst, const fc2t2_plan *plans, const std
     return FC2T2_OK;
 }
 
+// The batch after every instance's first part: the streams of the occupied-cell instances are
+// joined into s (the other instances' streams, forked with `mark`, run on), their shared M2L is
+// launched on s, and their streams are forked again for L2L and L2P (finish(i, plan)) and joined.
+static fc2t2_status occ_batch_after(int n_inst, const fc2t2_plan *plans, const std::vector<char> &joins, cudaStream_t s,
+                                    uint64_t mark, const std::function<fc2t2_status(int, fc2t2_plan_s *)> &finish) {
+    std::vector<fc2t2_plan> sub;
+    for (int i = 0; i < n_inst; ++i)
+        if (joins[i]) sub.push_back(plans[i]);
+    fc2t2_status st = batch_join((int)sub.size(), sub.data(), s, mark);
+    if (st == FC2T2_OK) st = occ_batch_m2l(n_inst, plans, joins, s);
+    if (st != FC2T2_OK) return st;
+    const uint64_t mark2 = ++g_batch_counter;
+    st = batch_fork((int)sub.size(), sub.data(), s, mark2);
+    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
+        if (joins[i]) st = finish(i, plans[i]);
+    const fc2t2_status sj = batch_join((int)sub.size(), sub.data(), s, mark2);
+    return st != FC2T2_OK ? st : sj;
+}
+
 fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *stream, const float *const *p,
                                    const float *const *w, const int64_t *N, const float *const *q, const int64_t *M,
                                    float *const *y) {
@@ -1090,21 +1110,16 @@ fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *st
         st = joins[i] ? occ_prepare(pl, pl->run, p[i], w[i], N[i], pl->src, q[i], nullptr, M[i], pl->qry)
                       : fc2t2_forward(pl, pl->run, p[i], w[i], N[i], q[i], M[i], y[i]);
     }
-    fc2t2_status sj = batch_join(n_inst, plans, s, mark);
-    if (st != FC2T2_OK || sj != FC2T2_OK || !any) return st != FC2T2_OK ? st : sj;
-    if ((st = occ_batch_m2l(n_inst, plans, joins, s)) != FC2T2_OK) return st;
-    mark = ++g_batch_counter;
-    std::vector<fc2t2_plan> sub;
-    for (int i = 0; i < n_inst; ++i)
-        if (joins[i]) sub.push_back(plans[i]);
-    st = batch_fork((int)sub.size(), sub.data(), s, mark);
-    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
-        if (joins[i]) {
-            fc2t2_plan_s *pl = plans[i];
-            st = occ_finish(pl, pl->run, pl->qry, M[i], y[i], nullptr);
-            pl->src.held_w = w[i];
-        }
-    sj = batch_join((int)sub.size(), sub.data(), s, mark);
+    if (st != FC2T2_OK || !any) {
+        const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+        return st != FC2T2_OK ? st : sj;
+    }
+    st = occ_batch_after(n_inst, plans, joins, s, mark, [&](int i, fc2t2_plan_s *pl) {
+        const fc2t2_status r = occ_finish(pl, pl->run, pl->qry, M[i], y[i], nullptr);
+        pl->src.held_w = w[i];
+        return r;
+    });
+    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);   // the other instances' streams
     return st != FC2T2_OK ? st : sj;
 }
 
@@ -1142,20 +1157,14 @@ static fc2t2_status backward_batched(int n_inst, const fc2t2_plan *plans, void *
         else
             st = fc2t2_backward(pl, pl->run, p[i], w[i], N[i], q[i], M[i], ybar[i], wbar[i], pbar[i]);
     }
-    fc2t2_status sj = batch_join(n_inst, plans, s, mark);
-    if (st != FC2T2_OK || sj != FC2T2_OK || !any) return st != FC2T2_OK ? st : sj;
-    if ((st = occ_batch_m2l(n_inst, plans, joins, s)) != FC2T2_OK) return st;
-    mark = ++g_batch_counter;
-    std::vector<fc2t2_plan> sub;
-    for (int i = 0; i < n_inst; ++i)
-        if (joins[i]) sub.push_back(plans[i]);
-    st = batch_fork((int)sub.size(), sub.data(), s, mark);
-    for (int i = 0; i < n_inst && st == FC2T2_OK; ++i)
-        if (joins[i]) {
-            fc2t2_plan_s *pl = plans[i];
-            st = occ_finish(pl, pl->run, pl->src, N[i], wbar[i], pbar[i]);
-        }
-    sj = batch_join((int)sub.size(), sub.data(), s, mark);
+    if (st != FC2T2_OK || !any) {
+        const fc2t2_status sj = batch_join(n_inst, plans, s, mark);
+        return st != FC2T2_OK ? st : sj;
+    }
+    st = occ_batch_after(n_inst, plans, joins, s, mark, [&](int i, fc2t2_plan_s *pl) {
+        return occ_finish(pl, pl->run, pl->src, N[i], wbar[i], pbar[i]);
+    });
+    const fc2t2_status sj = batch_join(n_inst, plans, s, mark);   // the other instances' streams
     return st != FC2T2_OK ? st : sj;
 }
 

@@ -316,19 +316,36 @@ __device__ __forceinline__ void occ_append(int *list, int *cnt, int cls, int cap
     list[(int64_t)cls * cap + base + __popc(peers & ((1u << lane) - 1u))] = cell;
 }
 
+// The cell of thread i of an occupancy kernel (n cells per dimension): the threads walk each
+// parity class in turn, a class's cells in blocks of 4 x 4 x 2 class positions (8 x 4 in 2D), so a
+// warp's appends -- and hence a work item's 32 consecutive targets -- are spatial neighbours.  Their
+// sets of occupied source cells then nearly coincide (the M2L warp runs their union) and their
+// source rows overlap in L1.
+template <int D>
+__device__ __forceinline__ int occ_cell(int i, int n, int G, int &cls) {
+    const int per_cls = G >> D, h = n >> 1;   // class positions: h per dimension
+    cls = i / per_cls;
+    const int r = i - cls * per_cls;
+    const int BX = min(D == 3 ? 4 : 8, h), BY = min(4, h), BZ = D == 3 ? min(2, h) : 1;
+    const int per = BX * BY * BZ, b = r / per, w = r - b * per;
+    const int nbx = h / BX, nby = h / BY;
+    const int ax = (b % nbx) * BX + w % BX, ay = ((b / nbx) % nby) * BY + (w / BX) % BY;
+    const int az = D == 3 ? (b / (nbx * nby)) * BZ + w / (BX * BY) : 0;
+    return (2 * ax + (cls & 1)) + n * ((2 * ay + ((cls >> 1) & 1)) + n * (D == 3 ? 2 * az + ((cls >> 2) & 1) : 0));
+}
+
 // finest level: occupancy from the sorts' counts (NULL: every cell occupied) and the target list
 template <int D>
 __global__ void __launch_bounds__(256) k_occ_fine(const int *__restrict__ src_cnt, const int *__restrict__ tgt_cnt,
                                                   unsigned char *__restrict__ act, int *__restrict__ list,
                                                   int *__restrict__ cnt, int n, int G) {
-    const int c = (int)(blockIdx.x * 256 + threadIdx.x);
-    const bool live = c < G;
-    int a = 0, cls = 0;
+    const int i = (int)(blockIdx.x * 256 + threadIdx.x);
+    const bool live = i < G;
+    int a = 0, cls = 0, c = 0;
     if (live) {
+        c = occ_cell<D>(i, n, G, cls);
         a = ((src_cnt == nullptr || src_cnt[c] > 0) ? 1 : 0) | ((tgt_cnt == nullptr || tgt_cnt[c] > 0) ? 2 : 0);
         act[c] = (unsigned char)a;
-        const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
-        cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
     }
     occ_append(list, cnt, cls, G >> D, c, live && (a & 2));
 }
@@ -337,10 +354,11 @@ __global__ void __launch_bounds__(256) k_occ_fine(const int *__restrict__ src_cn
 template <int D>
 __global__ void __launch_bounds__(256) k_occ_up(const unsigned char *__restrict__ child, unsigned char *__restrict__ act,
                                                 int *__restrict__ list, int *__restrict__ cnt, int n, int G) {
-    const int c = (int)(blockIdx.x * 256 + threadIdx.x);
-    const bool live = c < G;
-    int a = 0, cls = 0;
+    const int i = (int)(blockIdx.x * 256 + threadIdx.x);
+    const bool live = i < G;
+    int a = 0, cls = 0, c = 0;
     if (live) {
+        c = occ_cell<D>(i, n, G, cls);
         const int x = c % n, y = (c / n) % n, z = D == 3 ? c / (n * n) : 0;
         const int64_t nc = 2 * n;
 #pragma unroll
@@ -351,7 +369,6 @@ __global__ void __launch_bounds__(256) k_occ_up(const unsigned char *__restrict_
                 a |= child[base] | child[base + 1];
             }
         act[c] = (unsigned char)a;
-        cls = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2);
     }
     occ_append(list, cnt, cls, G >> D, c, live && (a & 2));
 }
