@@ -42,10 +42,11 @@ UNIT = "query-evals/s"
 TF32_PER_BF16 = 1.1 / 2.25
 # DRAM bytes (read + write) of one transform's M2L launches of the current kernel builds, from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum over the transform's M2L launches, on
-# the same grid and order at 2^18 points: the M2L launches do not depend on the point count);
-# None where no capture of the current build exists
-M2L_TRAFFIC_BYTES = {"separable": 1078485760.0,
-                     "bf16x3": (464.0 + 82.8) * 1e6}
+# the same grid and order at 2^18 points: the M2L launches do not depend on the point count), by
+# (M2L form, finest grid, coefficients per cell); None where no capture of the current build
+# exists for that form, grid and order
+M2L_TRAFFIC_BYTES = {("separable", 64, 84): 1078485760.0,
+                     ("bf16x3", 64, 84): (464.0 + 82.8) * 1e6}
 
 
 def parse():
@@ -448,7 +449,7 @@ def roofline_for(m: Measured, peaks):
         gbs = algo / (m2l_ms / 1e3) / 1e9
         inter = 2 * separable_bytes(m.info["coefficients"], m.info["levels"], m.grid)        # per step
         gbs_inter = inter / (m2l_ms / 1e3) / 1e9
-        traffic = M2L_TRAFFIC_BYTES.get("separable")
+        traffic = M2L_TRAFFIC_BYTES.get(("separable", m.grid, m.info["coefficients"]))
         return {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
                 "traffic": traffic, "traffic_unit": "bytes per transform (its M2L launches)",
                 "traffic_ratio": None if traffic is None else traffic / (algo / 2),
@@ -475,7 +476,8 @@ def roofline_for(m: Measured, peaks):
         basis += " x nominal TF32/BF16 ratio 1.1/2.25"
     executed = issued / (m2l_ms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-            "traffic": M2L_TRAFFIC_BYTES.get(m.mode), "traffic_unit": "bytes per launch (one transform)",
+            "traffic": M2L_TRAFFIC_BYTES.get((m.mode, m.grid, m.info["coefficients"])),
+            "traffic_unit": "bytes per launch (one transform)",
             "kernel": f"k_m2l_tc (tcgen05, {m.mode})", "flops_per_step": useful,
             "executed": {"flops_per_step": issued, "achieved": executed, "frac": executed / peak},
             "peak_basis": basis}
