@@ -707,8 +707,9 @@ def measure_fit(dev, flush, steps, n=1 << 24, adam_steps=100, n_ref=2048, check=
 def measure_batched(dev, flush, steps, warmup, n_inst=64):
     """The batched workload: 64 independent clustered point sets (N_i = M_i log-uniform in
     [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3), order (4, 6 or 8) and M2L form
-    (separable line passes over the whole grid, or the occupied-cell work queue) chosen by the
-    autotuner (fastest candidate within 1e-2 rel-L2 of the exact sum).  A step is one batched
+    (separable line passes over the whole grid, at the automatic or 32 finest-level cells per CTA,
+    or the occupied-cell work queue) chosen by the autotuner (fastest candidate within 1e-2 rel-L2
+    of the exact sum).  A step is one batched
     forward and one batched backward call over all instances: each instance's sorts, P2M and M2M on
     its plan's stream, one persistent M2L launch for all occupied-cell instances of an order, then
     L2L and L2P per instance; the same instances run one call after another on one stream for
@@ -723,10 +724,10 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     qs = [torch.from_numpy(wl.q).to(dev) for wl in wls]
     t0 = time.time()
     choices = [autotune.autotune(p, w, q, wl.sigma, target=1e-2, grids=(32, 64), orders=(4, 6, 8),
-                                 m2l=("occupied", "separable"), sample=512, reps=1)[0]
+                                 m2l=("occupied", "separable"), sample=512, reps=1, tiles=(0, 32))[0]
                for wl, p, w, q in zip(wls, ps, ws, qs)]
     tune_s = time.time() - t0
-    plans = [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, device=dev)
+    plans = [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, tile=c.tile, device=dev)
              for c, wl in zip(choices, wls)]
     stream = torch.cuda.current_stream(dev)
 
@@ -759,7 +760,7 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     queries = sum(wl.M for wl in wls)
     hist = {}
     for c in choices:
-        key = f"{c.grid}^3 order {c.order} {c.m2l}"
+        key = f"{c.grid}^3 order {c.order} {c.m2l}" + (f" tile {c.tile}" if c.tile else "")
         hist[key] = hist.get(key, 0) + 1
     for pl in plans:
         pl.close()

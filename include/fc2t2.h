@@ -125,6 +125,12 @@ typedef struct {
                                     accurate when cells are wide next to the kernel).  Not with the
                                     SEPARABLE M2L (UNSUPPORTED): the fit does not factor per
                                     dimension. */
+    int tile;                    /* SEPARABLE M2L, finest level: the cells per CTA along a pass's
+                                    axis (the line segment a CTA stages and computes).  0: 64 where
+                                    a CTA's shared memory allows it, else the longest that does;
+                                    16, 32 or 64: at most that many.  Other values: INVALID_ARG.  A
+                                    tuning knob only (every value gives the same result); ignored by
+                                    the other M2L forms. */
 } fc2t2_plan_desc;
 
 /* Build a plan: validate `desc`, build the M2L operator tables (the kernel's derivatives per

@@ -21,6 +21,7 @@ class Candidate:
     m2l: str
     ms: float              # forward + backward, milliseconds
     err: float             # relative L2 error of y against the exact sum on the query sample
+    tile: int = 0          # separable M2L: finest-level cells per CTA (0: the plan's automatic choice)
 
 
 def select(cands: Sequence[Candidate], target: float) -> Candidate:
@@ -38,13 +39,14 @@ def _rel_l2(a, b) -> float:
     return float(torch.linalg.vector_norm(a - b) / torch.clamp(torch.linalg.vector_norm(b), min=1e-300))
 
 
-def measure(p, w, q, sigma: float, grid: int, order: int, m2l: str, sample, ref, reps: int = 3) -> Candidate:
+def measure(p, w, q, sigma: float, grid: int, order: int, m2l: str, sample, ref, reps: int = 3,
+            tile: int = 0) -> Candidate:
     """Time a forward + backward step of one candidate and its error on the query sample."""
     import torch
     from .transform import Plan
     dim = p.shape[1]
     plan = Plan(dim, grid, order, sigma, m2l=m2l, max_sources=max(p.shape[0], 1),
-                max_queries=max(q.shape[0], 1), device=p.device)
+                max_queries=max(q.shape[0], 1), tile=tile, device=p.device)
     try:
         y = plan.forward(p, w, q)
         plan.backward(p, w, q, y)
@@ -58,7 +60,7 @@ def measure(p, w, q, sigma: float, grid: int, order: int, m2l: str, sample, ref,
         torch.cuda.synchronize(p.device)
         plan.check()
         err = _rel_l2(y[sample], ref)
-        return Candidate(grid, order, m2l, a.elapsed_time(b) / reps, err)
+        return Candidate(grid, order, m2l, a.elapsed_time(b) / reps, err, tile)
     finally:
         plan.close()
 
@@ -70,15 +72,16 @@ FP32_FORMS = ("fp32", "separable", "occupied", "tf32x3", "bf16x3")
 
 def autotune(p, w, q, sigma: float, target: float = 1e-2, grids: Iterable[int] = (32, 64),
              orders: Iterable[int] = (4, 6, 8), m2l: Iterable[str] = ("separable", "occupied"), sample: int = 1024,
-             seed: int = 0, reps: int = 3) -> Tuple[Candidate, List[Candidate]]:
-    """Measure the (grid, order, M2L form) candidates on the instance (p, w, q) and choose one.
+             seed: int = 0, reps: int = 3, tiles: Iterable[int] = (0,)) -> Tuple[Candidate, List[Candidate]]:
+    """Measure the (grid, order, M2L form, tile) candidates on the instance (p, w, q) and choose one.
 
     The forms differ in how the M2L's work is laid out on the GPU: the separable line passes
-    sweep every cell of the grid, the occupied-cell form takes work items of 32 occupied target
-    cells from a queue (work in proportion to the occupied cell pairs).  ``sample`` queries
-    (seeded) are compared with the exact sum.  An FP32-accurate form of a (grid, order) whose
-    first FP32-accurate candidate missed the target is skipped (same operator, same error).
-    Returns (choice, every measured candidate)."""
+    sweep every cell of the grid in segments of ``tile`` cells per CTA at the finest level (each
+    value of ``tiles``; 0 is the plan's automatic choice), the occupied-cell form takes work items
+    of 32 occupied target cells from a queue (work in proportion to the occupied cell pairs).
+    ``sample`` queries (seeded) are compared with the exact sum.  An FP32-accurate candidate of a
+    (grid, order) whose first FP32-accurate candidate missed the target is skipped (same operator,
+    same error).  Returns (choice, every measured candidate)."""
     from .transform import direct
     M = q.shape[0]
     rng = np.random.default_rng(seed)
@@ -92,11 +95,12 @@ def autotune(p, w, q, sigma: float, target: float = 1e-2, grids: Iterable[int] =
         for o in orders:
             missed = False
             for f in m2l:
-                if missed and f in FP32_FORMS:
-                    continue
-                c = measure(p, w, q, sigma, g, o, f, sample_idx, ref, reps)
-                cands.append(c)
-                missed = missed or (f in FP32_FORMS and c.err > target)
+                for t in (tuple(tiles) if f == "separable" else (0,)):
+                    if missed and f in FP32_FORMS:
+                        continue
+                    c = measure(p, w, q, sigma, g, o, f, sample_idx, ref, reps, tile=t)
+                    cands.append(c)
+                    missed = missed or (f in FP32_FORMS and c.err > target)
     return select(cands, target), cands
 
 

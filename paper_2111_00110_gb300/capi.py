@@ -73,6 +73,7 @@ class PlanDesc(ctypes.Structure):
         ("max_sources", ctypes.c_int64),
         ("max_queries", ctypes.c_int64),
         ("fit", ctypes.c_int),
+        ("tile", ctypes.c_int),
     ]
 
 

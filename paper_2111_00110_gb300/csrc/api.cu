@@ -378,6 +378,8 @@ static fc2t2_status validate_desc(const fc2t2_plan_desc *d) {
     if (d->m2l == FC2T2_M2L_SEPARABLE && (d->kernel != FC2T2_KERNEL_GAUSSIAN || d->dim != 3))
         return set_error(FC2T2_ERR_UNSUPPORTED, "the separable M2L needs the Gaussian kernel and dim = 3");
     if (d->fit != 0 && d->fit != 1) return set_error(FC2T2_ERR_INVALID_ARG, "fit must be 0 or 1");
+    if (d->tile != 0 && d->tile != 16 && d->tile != 32 && d->tile != 64)
+        return set_error(FC2T2_ERR_INVALID_ARG, "tile must be 0, 16, 32 or 64");
     if (d->fit && d->m2l == FC2T2_M2L_SEPARABLE)
         return set_error(FC2T2_ERR_UNSUPPORTED, "fitted operators do not factor per dimension (no separable M2L)");
     if (d->max_sources < 0 || d->max_queries < 0 || d->max_sources > (int64_t)INT32_MAX ||

@@ -658,7 +658,8 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
     // 32 target pairs), 32, 16, 8, 4 cells that keeps every pass's CTA within 116 KB of shared
     // memory at orders <= 6 (two or three CTAs per multiprocessor) and 220 KB at orders 7-8 (one:
     // there the longer segments' smaller halo share outweighs the lost CTA, order 8 M2L 2.99 ->
-    // 2.72 ms per step); segments shorter than a warp split warps between tasks
+    // 2.72 ms per step); segments shorter than a warp split warps between tasks.  The plan's
+    // `tile` caps the finest level's length (a tuning knob)
     size_t max_smem = 0;
     const size_t cap = (size_t)(pl->rho >= 7 ? 220 : 116) * 1024;
     for (int l = 0; l < pl->nlev; ++l) {
@@ -666,6 +667,7 @@ fc2t2_status build_sep(fc2t2_plan_s *pl, const std::vector<double> &dtab64) {
         int seg = 4;
         for (int cand : {64, 32, 16, 8}) {
             if (cand > n || (cand == 64 && l != 0)) continue;
+            if (l == 0 && pl->desc.tile > 0 && cand > pl->desc.tile) continue;
             bool fits = true;
             for (int axis = 0; axis < 3; ++axis) {
                 const int ip = axis == 0 ? pl->Pp : Q4p, op = axis == 2 ? pl->Pp : Q4p;

@@ -52,7 +52,7 @@ class Plan:
                  kernel: str = "gaussian", poly_coef: Optional[Sequence[float]] = None,
                  lo: float = 0.0, hi: float = 1.0, m2l: str = "auto", check_domain: bool = False,
                  max_sources: int = 1 << 20, max_queries: int = 1 << 20, channels: int = 1, fit: bool = False,
-                 device=None):
+                 tile: int = 0, device=None):
         self.dim, self.grid, self.order, self.channels = dim, grid, order, int(channels)
         m2l = resolve_m2l(m2l, dim, kernel, fit)
         self._serial = 0   # counts the calls that replace the plan's expansion
@@ -73,6 +73,8 @@ class Plan:
         d.m2l = capi.M2L_PREC[m2l]
         d.check_domain = 1 if check_domain else 0
         d.fit = 1 if fit else 0   # least-squares fitted M2L operators (Sec. 3.1)
+        d.tile = int(tile)        # separable M2L: finest-level cells per CTA (0: automatic)
+        self.tile = int(tile)
         d.max_sources, d.max_queries = self.max_sources, self.max_queries
         with torch.cuda.device(self.device):
             self._h = capi.plan_create(d)

@@ -28,3 +28,9 @@ def test_ties_in_time_prefer_accuracy():
 def test_empty():
     with pytest.raises(ValueError):
         select([], 1e-2)
+
+
+def test_candidates_carry_their_tile():
+    a = Candidate(64, 6, "separable", 1.0, 5e-3, tile=32)
+    b = Candidate(64, 6, "separable", 1.1, 5e-3)
+    assert select([a, b], 1e-2).tile == 32 and b.tile == 0

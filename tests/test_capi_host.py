@@ -107,3 +107,10 @@ def test_m2l_form_names_match_the_header():
     vals = {m.group(1).lower(): int(m.group(2)) for m in re.finditer(r"FC2T2_M2L_(\w+)\s*=\s*(\d+)", text)}
     assert vals == capi.M2L_PREC
     assert vals["occupied"] == 6
+
+
+@pytest.mark.parametrize("tile", [1, 8, 48, 128, -16])
+def test_tile_values_are_checked(lib, tile):
+    out = ctypes.c_void_p(123)
+    assert lib.fc2t2_plan_create(ctypes.byref(_desc(m2l=5, tile=tile)), ctypes.byref(out)) == 1
+    assert out.value is None

@@ -254,6 +254,26 @@ def test_direct_sum_matches_the_oracle(lib):
         assert rel_l2(y.cpu().numpy(), yo) <= 1e-6
 
 
+@pytest.mark.parametrize("grid,order", [(64, 6), (32, 8)])
+def test_separable_tile_gives_the_same_transform(lib, grid, order):
+    """The separable M2L's finest-level cells per CTA (the plan's tile) changes only how the line
+    passes are cut into CTAs: every tile gives the automatic tile's result to rounding and the
+    oracle's within the FP32 bar."""
+    from paper_2111_00110_gb300.transform import Plan
+    wl = workloads.mixture(21, grid=grid, order=order, n_override=6000)
+    p, w, q = dev(wl.p), dev(wl.w), dev(wl.q)
+    ys = {}
+    for tile in (0, 16, 32, 64):
+        plan = Plan(3, grid, order, wl.sigma, m2l="separable", max_sources=wl.N, max_queries=wl.M, tile=tile)
+        ys[tile] = plan.forward(p, w, q).cpu().numpy()
+        plan.check()
+        plan.close()
+    for tile in (16, 32, 64):
+        assert rel_l2(ys[tile], ys[0]) <= 1e-6, tile
+    yo = oracle.forward(odesc(3, grid, order, wl.sigma), *f64(wl.p, wl.w, wl.q))
+    assert_close(ys[32], yo, what=f"tile 32, n{grid} rho{order}")
+
+
 def test_autotune_meets_the_target_on_a_batch_instance(lib):
     """Grid, order and M2L form chosen per instance: the choice meets the error target against the
     exact sum and is the fastest candidate that does; a second FP32 form of a (grid, order) whose
@@ -261,7 +281,7 @@ def test_autotune_meets_the_target_on_a_batch_instance(lib):
     from paper_2111_00110_gb300.autotune import autotune
     wl = workloads.mixture(3, n_override=30000)
     choice, cands = autotune(dev(wl.p), dev(wl.w), dev(wl.q), 0.02, target=1e-2, grids=(32, 64),
-                             orders=(4, 6, 8), m2l=("separable", "occupied"), sample=512)
+                             orders=(4, 6, 8), m2l=("separable", "occupied"), sample=512, tiles=(0, 32))
     print([(c.grid, c.order, c.m2l, round(c.ms, 3), f"{c.err:.2e}") for c in cands], "->",
           (choice.grid, choice.order, choice.m2l))
     assert choice.err <= 1e-2
@@ -271,10 +291,11 @@ def test_autotune_meets_the_target_on_a_batch_instance(lib):
         by.setdefault((c.grid, c.order), []).append(c)
     assert sorted(by) == [(g, o) for g in (32, 64) for o in (4, 6, 8)]
     for cs in by.values():
-        assert cs[0].m2l == "separable"
-        assert len(cs) == (1 if cs[0].err > 1e-2 else 2)
-        if len(cs) == 2:   # the two FP32 forms of one operator agree to rounding
-            assert abs(cs[0].err - cs[1].err) <= 1e-4 * cs[0].err
+        assert cs[0].m2l == "separable" and cs[0].tile == 0
+        assert len(cs) == (1 if cs[0].err > 1e-2 else 3)   # separable tiles 0 and 32, occupied
+        if len(cs) == 3:   # the FP32 forms of one operator agree to rounding
+            assert cs[1].tile == 32 and cs[2].m2l == "occupied"
+            assert all(abs(c.err - cs[0].err) <= 1e-4 * cs[0].err for c in cs)
     # the error falls with the order on the finer grid (truncation, Sec. 3)
     errs = {(c.grid, c.order): c.err for c in cands}
     assert errs[(64, 8)] < errs[(64, 4)]
