@@ -712,8 +712,8 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     of the exact sum).  A step is one batched
     forward and one batched backward call over all instances: each instance's sorts, P2M and M2M on
     its plan's stream, one persistent M2L launch for all occupied-cell instances of an order, then
-    L2L and L2P per instance; the same instances run one call after another on one stream for
-    comparison."""
+    L2L and L2P per instance.  The step is captured in a CUDA graph and replayed; the same step
+    launched eagerly, and the instances one call after another on one stream, for comparison."""
     import time
     import torch
     from paper_2111_00110_gb300 import autotune, workloads
@@ -755,7 +755,19 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
             total += a.elapsed_time(b)
         return total / steps
 
-    ms = timed(step_batched)
+    ms_eager = timed(step_batched)
+    # the batched step captured once in a CUDA graph (every instance's launches, the plan streams'
+    # fork / join and the shared M2L launches recorded once) and replayed
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        step_batched()
+    stream.wait_stream(side)
+    torch.cuda.synchronize(dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        step_batched()
+    ms = timed(graph.replay)
     ms_seq = timed(step_sequential)
     queries = sum(wl.M for wl in wls)
     hist = {}
@@ -767,7 +779,8 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     return {"workload": f"mixture, {n_inst} instances", "instances": n_inst, "queries": queries,
             "sigma": wls[0].sigma, "choices": hist, "autotune_s": tune_s,
             "value": queries / (ms / 1e3), "unit": "query-evals/s (fwd+bwd, all instances)",
-            "ms_per_step": ms, "steps": steps,
+            "ms_per_step": ms, "steps": steps, "timed": "the batched step replayed from a CUDA graph",
+            "eager": {"ms_per_step": ms_eager, "value": queries / (ms_eager / 1e3)},
             "one_stream": {"ms_per_step": ms_seq, "value": queries / (ms_seq / 1e3)}}
 
 
