@@ -713,7 +713,8 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     [1024, 262144]), sigma 0.02, each with its grid (32^3 or 64^3), order (4, 6 or 8) and M2L form
     (separable line passes over the whole grid, at the automatic or 32 finest-level cells per CTA,
     or the occupied-cell work queue) chosen by the autotuner (fastest candidate within 1e-2 rel-L2
-    of the exact sum).  A step is one batched
+    of the exact sum), then refined for the batch (the choices timed as a whole batch against the
+    same with the FP32 forms moved to the occupied-cell form).  A step is one batched
     forward and one batched backward call over all instances: each instance's sorts, P2M and M2M on
     its plan's stream, one persistent M2L launch for all occupied-cell instances of an order, then
     L2L and L2P per instance.  The step is captured in a CUDA graph and replayed; the same step
@@ -730,10 +731,34 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     choices = [autotune.autotune(p, w, q, wl.sigma, target=1e-2, grids=(32, 64), orders=(4, 6, 8),
                                  m2l=("occupied", "separable"), sample=512, reps=1, tiles=(0, 32))[0]
                for wl, p, w, q in zip(wls, ps, ws, qs)]
-    tune_s = time.time() - t0
-    plans = [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, tile=c.tile, device=dev)
-             for c, wl in zip(choices, wls)]
     stream = torch.cuda.current_stream(dev)
+
+    def make_plans(cs):
+        return [Plan(3, c.grid, c.order, wl.sigma, m2l=c.m2l, max_sources=wl.N, max_queries=wl.M, tile=c.tile,
+                     device=dev) for c, wl in zip(cs, wls)]
+
+    def time_batch(cs, reps=3):
+        pls = make_plans(cs)
+        try:
+            for _ in range(2):
+                backward_batched(pls, ps, ws, qs, forward_batched(pls, ps, ws, qs), reuse_forward=True)
+            torch.cuda.synchronize(dev)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                backward_batched(pls, ps, ws, qs, forward_batched(pls, ps, ws, qs), reuse_forward=True)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            return a.elapsed_time(b) / reps
+        finally:
+            for pl in pls:
+                pl.close()
+
+    # the per-instance choices against the same with the FP32 forms on the occupied-cell form
+    # (one shared M2L launch), timed as whole batches
+    choices, refinement = autotune.refine_batch(choices, time_batch)
+    tune_s = time.time() - t0
+    plans = make_plans(choices)
 
     def step_batched():
         ys = forward_batched(plans, ps, ws, qs)
@@ -781,7 +806,7 @@ def measure_batched(dev, flush, steps, warmup, n_inst=64):
     for pl in plans:
         pl.close()
     return {"workload": f"mixture, {n_inst} instances", "instances": n_inst, "queries": queries,
-            "sigma": wls[0].sigma, "choices": hist, "autotune_s": tune_s,
+            "sigma": wls[0].sigma, "choices": hist, "autotune_s": tune_s, "batch_refinement": refinement,
             "value": queries / (ms / 1e3), "unit": "query-evals/s (fwd+bwd, all instances)",
             "ms_per_step": ms, "steps": steps, "timed": "the batched step replayed from a CUDA graph",
             "eager": {"ms_per_step": ms_eager, "value": queries / (ms_eager / 1e3)},

@@ -8,8 +8,8 @@ selection rule is separate from the measurements so that it can be checked on th
 """
 from __future__ import annotations
 
-from dataclasses import dataclass
-from typing import Iterable, List, Optional, Sequence, Tuple
+from dataclasses import dataclass, replace
+from typing import Callable, Iterable, List, Optional, Sequence, Tuple
 
 import numpy as np
 
@@ -102,6 +102,23 @@ def autotune(p, w, q, sigma: float, target: float = 1e-2, grids: Iterable[int] =
                     cands.append(c)
                     missed = missed or (f in FP32_FORMS and c.err > target)
     return select(cands, target), cands
+
+
+def refine_batch(choices: Sequence[Candidate], time_batch: Callable[[Sequence[Candidate]], float]):
+    """Batch-level refinement of per-instance choices.
+
+    An instance timed alone does not see the batch: in a batched call the occupied-cell instances
+    share one M2L launch, which an instance on another form does not join.  So the per-instance
+    choices are timed as a whole batch (``time_batch(choices)``: ms per batched step) against the
+    same choices with every FP32-accurate form moved to the occupied-cell form at the same grid and
+    order (the same operator, hence the same error against the exact sum); the faster is kept.
+    Returns (choices, {"per_instance_ms": ..., "occupied_ms": ...} or {} when nothing moves)."""
+    alt = [replace(c, m2l="occupied", tile=0) if (c.m2l in FP32_FORMS and c.m2l != "occupied") else c
+           for c in choices]
+    if alt == list(choices):
+        return list(choices), {}
+    t_own, t_alt = time_batch(choices), time_batch(alt)
+    return (alt if t_alt < t_own else list(choices)), {"per_instance_ms": t_own, "occupied_ms": t_alt}
 
 
 def tune_batch(instances, sigma: float, target: float = 1e-2, **kw) -> List[Candidate]:
