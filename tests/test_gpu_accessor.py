@@ -64,7 +64,7 @@ def f64(*a):
 # ------------------------------------------------------------------------------- channels
 
 @pytest.mark.parametrize("dim,grid,order,m2l", [(3, 16, 4, "fp32"), (3, 16, 6, "separable"), (2, 32, 4, "fp32"),
-                                                (3, 16, 5, "bf16x3")])
+                                                (3, 16, 5, "bf16x3"), (3, 16, 6, "occupied"), (2, 32, 5, "occupied")])
 def test_channels_forward_backward(lib, dim, grid, order, m2l):
     """y[c], wbar[c] per channel and pbar, qbar summed over channels against the oracle run per
     channel; each channel agrees with a one-channel plan's transform of its weights."""
@@ -144,7 +144,7 @@ def test_channels_direct_and_empty(lib):
 # ------------------------------------------------------------------------------ accessor
 
 ACC_CASES = [(3, 16, 4, "fp32", 1), (3, 16, 6, "separable", 2), (3, 8, 8, "fp32", 1), (3, 16, 1, "fp32", 1),
-             (2, 32, 4, "fp32", 3), (2, 16, 8, "fp32", 1), (3, 16, 6, "bf16x3", 1)]
+             (2, 32, 4, "fp32", 3), (2, 16, 8, "fp32", 1), (3, 16, 6, "bf16x3", 1), (3, 16, 6, "occupied", 2)]
 
 
 @pytest.mark.parametrize("dim,grid,order,m2l,C", ACC_CASES)

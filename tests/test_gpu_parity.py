@@ -478,7 +478,8 @@ def test_l2p_without_finest_l2l_matches_l2l(lib, dim, order, m2l):
 # ------------------------------------------------------- least-squares fitted operators
 
 @pytest.mark.parametrize("dim,grid,order,m2l", [(3, 8, 4, "fp32"), (3, 16, 6, "bf16x3"), (3, 16, 5, "tf32x3"),
-                                                (2, 16, 4, "fp32"), (3, 8, 6, "tf32")])
+                                                (2, 16, 4, "fp32"), (3, 8, 6, "tf32"), (3, 16, 4, "occupied"),
+                                                (2, 16, 6, "occupied")])
 def test_fitted_operators(lib, dim, grid, order, m2l):
     """M2L with least-squares fitted coefficients (Sec. 3.1) against the oracle's own fit, forward
     and backward; with cells wider than the kernel the fitted transform is closer to the exact sum

@@ -64,7 +64,7 @@ def scene(seed, N, width, extra):
 
 
 @pytest.mark.parametrize("grid,order,m2l", [(16, 4, "fp32"), (16, 6, "separable"), (8, 8, "fp32"),
-                                            (32, 5, "separable"), (16, 6, "bf16x3")])
+                                            (32, 5, "separable"), (16, 6, "bf16x3"), (16, 6, "occupied")])
 def test_ray_forward_and_adjoint(lib, grid, order, m2l):
     from paper_2111_00110_gb300.transform import Plan
     p, w, rays = scene(200 + order, 3000, 24, 300)
