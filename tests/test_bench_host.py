@@ -103,3 +103,31 @@ def test_reference_arm_prints_one_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["cpu_baseline"]["cores"] >= 1 and d["cpu_baseline"]["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_forms_and_traffic_keys():
+    """The bench's roofline per M2L form: the CUDA-core forms (plain and occupied-cell) against the
+    FP32 ALU peak derived from the SM clock, the separable form against HBM with the DRAM-traffic
+    figure only where a capture of that form, grid and order exists, the tensor-core forms against
+    the measured BF16 peak (TF32 scaled)."""
+    import bench
+    peaks = {"hbm_gbs": 6000.0, "bf16_tflops_sustained": 1800.0, "sm_max_mhz": 2000.0}
+
+    def meas(mode, grid=64, P=84, levels=5):
+        m = bench.Measured()
+        m.mode, m.grid = mode, grid
+        m.stage_ms = {"m2l": 2.0}
+        m.info = {"m2l_useful_flops": 1e11, "m2l_issued_flops": 3e11, "coefficients": P, "levels": levels}
+        return m
+
+    for mode in ("fp32", "occupied"):
+        r = bench.roofline_for(meas(mode), peaks)
+        assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+        assert abs(r["achieved"] - 2 * 1e11 / 2e-3 / 1e12) < 1e-9       # two transforms per step
+        assert abs(r["peak"] - 152 * 128 * 2 * 2000e6 / 1e12) < 1e-6
+    assert "k_m2l_occ" in bench.roofline_for(meas("occupied"), peaks)["kernel"]
+    sep = bench.roofline_for(meas("separable"), peaks)
+    assert sep["bound"] == "hbm" and sep["traffic"] == bench.M2L_TRAFFIC_BYTES[("separable", 64, 84)]
+    assert bench.roofline_for(meas("separable", P=165, levels=5), peaks)["traffic"] is None   # order 8: no capture
+    tf = bench.roofline_for(meas("tf32"), peaks)
+    assert tf["bound"] == "tensor" and abs(tf["peak"] - 1800.0 * 1.1 / 2.25) < 1e-9 and tf["traffic"] is None
