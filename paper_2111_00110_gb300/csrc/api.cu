@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -1007,12 +1008,14 @@ static bool occ_batched(const fc2t2_plan_s *pl, int64_t n_src, int64_t n_tgt) {
     return pl->occ.enabled && pl->C == 1 && n_src > 0 && n_tgt > 0 && !pl->profiling;
 }
 
-// Whether the plan of instance i serves another instance of the batch too: its instances then run
-// one after another on the plan's stream (one workspace), none of them in the shared M2L launch.
-static bool plan_repeats(int n_inst, const fc2t2_plan *plans, int i) {
-    for (int k = 0; k < n_inst; ++k)
-        if (k != i && plans[k] == plans[i]) return true;
-    return false;
+// Per instance, whether its plan serves another instance of the batch too: those instances run one
+// after another on the plan's stream (one workspace), none of them in the shared M2L launch.
+static std::vector<char> plans_repeated(int n_inst, const fc2t2_plan *plans) {
+    std::unordered_map<const fc2t2_plan_s *, int> uses;
+    for (int i = 0; i < n_inst; ++i) ++uses[plans[i]];
+    std::vector<char> rep(n_inst);
+    for (int i = 0; i < n_inst; ++i) rep[i] = uses[plans[i]] > 1;
+    return rep;
 }
 
 // One instance of a batched transform up to its M2L: sorts of targets (tx, tw) and sources
@@ -1098,9 +1101,10 @@ fc2t2_status fc2t2_forward_batched(int n_inst, const fc2t2_plan *plans, void *st
     cudaStream_t s = (cudaStream_t)stream;
     // occupied-cell instances: sorts .. M2M on their streams, one M2L launch for all, then L2L, L2P
     std::vector<char> joins(n_inst, 0);
+    const std::vector<char> repeated = plans_repeated(n_inst, plans);
     bool any = false;
     for (int i = 0; i < n_inst; ++i) {
-        if (!occ_batched(plans[i], N[i], M[i]) || plan_repeats(n_inst, plans, i)) continue;
+        if (!occ_batched(plans[i], N[i], M[i]) || repeated[i]) continue;
         if (!p[i] || !w[i] || !q[i] || !y[i]) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
         joins[i] = 1;
         any = true;
@@ -1138,9 +1142,10 @@ static fc2t2_status backward_batched(int n_inst, const fc2t2_plan *plans, void *
     // occupied-cell instances (the transposed transform: sources q with weights ybar, targets p):
     // sorts .. M2M on their streams, one M2L launch for all, then L2L, L2P value and gradient
     std::vector<char> joins(n_inst, 0);
+    const std::vector<char> repeated = plans_repeated(n_inst, plans);
     bool any = false;
     for (int i = 0; i < n_inst; ++i) {
-        if (!occ_batched(plans[i], M[i], N[i]) || (!wbar[i] && !pbar[i]) || plan_repeats(n_inst, plans, i)) continue;
+        if (!occ_batched(plans[i], M[i], N[i]) || (!wbar[i] && !pbar[i]) || repeated[i]) continue;
         if (!p[i] || !w[i] || !q[i] || !ybar[i]) return set_error(FC2T2_ERR_INVALID_ARG, "NULL array");
         joins[i] = 1;
         any = true;
