@@ -1058,12 +1058,19 @@ static fc2t2_status occ_batch_m2l(int n_inst, const fc2t2_plan *plans, const std
         if (joins[i]) todo.push_back(plans[i]);
     while (!todo.empty()) {
         std::vector<const fc2t2_plan_s *> group, rest;
-        for (auto *pl : todo)
+        // the queue numbers its work chunks (of at least 32 targets) in 32-bit integers: a launch
+        // takes plans while their largest possible chunk count stays below 2^30
+        int64_t chunks = 0;
+        for (auto *pl : todo) {
+            const int64_t most = pl->G_total / 32 + kOccBuckets;
             if (pl->D == todo[0]->D && pl->rho == todo[0]->rho && (int)group.size() < kOccMaxInst &&
-                std::find(group.begin(), group.end(), pl) == group.end())
+                (group.empty() || chunks + most < ((int64_t)1 << 30))) {
                 group.push_back(pl);
-            else
+                chunks += most;
+            } else {
                 rest.push_back(pl);
+            }
+        }
         fc2t2_status st = check_cuda(launch_m2l_occ(group.data(), (int)group.size(), s), "m2l (occupied cells, batched)");
         if (st != FC2T2_OK) return st;
         todo.swap(rest);
