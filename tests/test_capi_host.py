@@ -114,3 +114,22 @@ def test_tile_values_are_checked(lib, tile):
     out = ctypes.c_void_p(123)
     assert lib.fc2t2_plan_create(ctypes.byref(_desc(m2l=5, tile=tile)), ctypes.byref(out)) == 1
     assert out.value is None
+
+
+@pytest.mark.parametrize("dim,kernel,fit", [(3, 0, 0), (2, 0, 1), (3, 1, 0)])
+def test_occupied_m2l_descriptors_pass_validation(lib, dim, kernel, fit):
+    """The occupied-cell M2L takes any kernel, 2D and 3D, and fitted operators: such a descriptor
+    passes the host checks (without a GPU the plan then fails at its first device step, with a
+    CUDA or memory error; with one it is built and released)."""
+    coef = (ctypes.c_double * 4)(*([1.0] * 4))   # degree-1 polynomial in 3D: C(4, 3) = 4
+    d = _desc(dim=dim, kernel=kernel, fit=fit, m2l=6)
+    if kernel == 1:
+        d.poly_coef = ctypes.cast(coef, ctypes.POINTER(ctypes.c_double))
+        d.n_poly = 4
+    out = ctypes.c_void_p(123)
+    st = lib.fc2t2_plan_create(ctypes.byref(d), ctypes.byref(out))
+    assert st in (0, 3, 5), st
+    if st == 0:
+        lib.fc2t2_plan_destroy(out)
+    else:
+        assert out.value is None
