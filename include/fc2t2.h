@@ -318,7 +318,10 @@ typedef struct {
     double m2l_cell_pairs;       /* interacting (target, source) cell pairs over all levels */
     double m2l_useful_flops;     /* 2 x #{(k, b): |k| + |b| <= order} x m2l_cell_pairs */
     double m2l_issued_flops;     /* multiply-add work (x2) the M2L kernels issue, incl. the zeros
-                                    inside the dense tensor-core blocks; = useful on CUDA cores */
+                                    inside the dense tensor-core blocks; = useful on CUDA cores.
+                                    For the OCCUPIED form both figures are those of every cell
+                                    pair: an upper bound (it runs the occupied pairs only, which
+                                    the points decide) */
     int64_t device_bytes;        /* device memory owned by the plan */
     int m2l_classes_per_cta;     /* target parity classes one tensor-core CTA accumulates (1, 2 or
                                     4; 0 when the M2L runs on the CUDA cores) */
